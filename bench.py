@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Throughput of the renderer on the 1M-Gaussian 1920x1080 workload.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step renders one full frame (preprocess -> cull -> sort -> render) of the
+1M-Gaussian cluster scene for one of 16 seeded camera poses (cycled), with
+the scene resident in HBM.  Each step is timed with CUDA events on the
+launching stream and L2 is flushed (a 256 MB write) between steps, outside the
+events.  Prints one JSON line (rank 0).  With torchrun (N > 1) every rank
+renders its own replica (frames are independent: weak scaling, no
+collective); the job value is the sum of frames over max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of pixels of the same frames and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s @1M Gaussians (fwd)"
+WORKLOAD = "scene1m: 1,000,000 Gaussians (64 clusters + 10% shell, SH 3), 1920x1080, 16 poses"
+
+# algorithmic FP32 operations per pixel x Gaussian evaluation in the render
+# kernel: 12 FMA (num, d) + 3 x 3 for |num|^2, |d|^2 (6 FMA, counted 2 ops) ...
+# see DESIGN.md "Render roofline" for the count.
+OPS_PER_EVAL = 36
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--capacity", type=int, default=48 << 20)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for name, v in zip(names, s[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def load_workload():
+    from paper_2504_12811_gb300 import scenes
+    t = time.time()
+    scene, poses = scenes.workload("scene1m")
+    return scene, poses, time.time() - t
+
+
+def cpu_baseline(scene, poses, seconds, unit_pixels):
+    """Time the oracle as it stands on a bounded pixel sample of pose 0.
+    Returns (frames/s equivalent, sample description, threads)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    cam = poses[0]
+    t0 = time.time()
+    prep = O.prepare(scene, cam)
+    t_prep = time.time() - t0
+    rng = np.random.default_rng(123)
+    done, t_pix = 0, 0.0
+    batch = 16
+    while t_pix < seconds and done < 4096:
+        px = rng.integers(0, cam.width, batch)
+        py = rng.integers(0, cam.height, batch)
+        t1 = time.time()
+        O.render_pixels(scene, cam, px, py, prep=prep)
+        t_pix += time.time() - t1
+        done += batch
+    per_pixel = t_pix / done
+    frame_s = t_prep + per_pixel * unit_pixels
+    desc = (f"pose 0: oracle preparation of all {scene.n} Gaussians ({t_prep:.2f} s) + "
+            f"{done} random pixels ({t_pix:.2f} s); frame time extrapolated to "
+            f"{unit_pixels} pixels")
+    return 1.0 / frame_s, desc, torch.get_num_threads(), frame_s
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    scene, poses, _ = load_workload()
+    W, H = poses[0].width, poses[0].height
+    import numpy as np
+    import oracle as O
+    rng = np.random.default_rng(5)
+    # each step: oracle preparation for the pose + a bounded pixel sample
+    pix = 16
+    frame_times = []
+    for step in range(args.warmup + args.steps):
+        cam = poses[step % len(poses)]
+        t0 = time.time()
+        prep = O.prepare(scene, cam)
+        t_prep = time.time() - t0
+        px = rng.integers(0, W, pix)
+        py = rng.integers(0, H, pix)
+        t1 = time.time()
+        O.render_pixels(scene, cam, px, py, prep=prep)
+        t_pix = time.time() - t1
+        if step >= args.warmup:
+            frame_times.append(t_prep + t_pix / pix * W * H)
+    mean_frame = sum(frame_times) / len(frame_times)
+    value = 1.0 / mean_frame
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean_frame * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": torch.get_num_threads(),
+                         "kind": "oracle",
+                         "sample": f"per step: oracle preparation of all Gaussians for the pose + {pix} "
+                                   f"random pixels, frame time extrapolated to {W * H} pixels"},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2504_12811_gb300 import aaag, build as B
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    scene, poses, t_gen = load_workload()
+    W, H = poses[0].width, poses[0].height
+    ds = aaag.DeviceScene(scene, device=dev)
+    ws = aaag.Workspace(scene.n, W, H, args.capacity, device=dev)
+    rgb = torch.empty(3, H, W, device=dev)
+    alpha = torch.empty(H, W, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    prm = aaag.make_params()
+    cams = [aaag.make_camera(c) for c in poses]
+    scene_struct = ds.struct()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def frame(i, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        aaag.aaag_preprocess(scene_struct, cams[i % len(cams)], prm, ws.handle, sptr)
+        if ev is not None:
+            ev[1].record(stream)
+        aaag.aaag_cull(ws.handle, sptr)
+        if ev is not None:
+            ev[2].record(stream)
+        aaag.aaag_sort(ws.handle, sptr)
+        if ev is not None:
+            ev[3].record(stream)
+        aaag.aaag_render(ws.handle, rgb.data_ptr(), alpha.data_ptr(), sptr)
+        if ev is not None:
+            ev[4].record(stream)
+
+    # warm-up (also checks capacity / timeouts once)
+    for i in range(max(args.warmup, 3)):
+        frame(i)
+    st = aaag.stats(ws, check=False)
+    if st["status"] != "OK":
+        raise SystemExit(f"warm-up frame failed: {st}")
+
+    # per-pose statistics (evaluations are needed for the roofline)
+    per_pose = []
+    for i in range(len(poses)):
+        frame(i)
+        per_pose.append(aaag.stats(ws, check=True))
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    wall0 = time.time()
+    for k in range(args.steps):
+        flush.zero_()                                  # evict L2 between steps
+        frame(args.warmup + k, evs[k])
+    torch.cuda.synchronize()
+    wall = time.time() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    stage = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(4)] for k in range(args.steps)])
+    step_ms = stage.sum(1)
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    frames = args.steps * world
+    value = frames / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (render, FP32 ALU bound)
+    ev_by_step = [per_pose[(args.warmup + k) % len(poses)]["evaluations"] for k in range(args.steps)]
+    render_ms = stage[:, 3]
+    achieved_tflops = float(np.sum(np.array(ev_by_step) * OPS_PER_EVAL) / (render_ms.sum() / 1e3) / 1e12)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    # preprocess + cull + sort: algorithmic bytes vs measured HBM peak
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_peak = float(peaks["hbm_gbs"])
+        hbm_src = "measured"
+    except (OSError, KeyError, ValueError):
+        hbm_peak, hbm_src = 6800.0, "fallback"
+    pre_bytes, sort_bytes = [], []
+    for k in range(args.steps):
+        s = per_pose[(args.warmup + k) % len(poses)]
+        V, K = s["n_visible"], s["n_pairs"]
+        pre_bytes.append(scene.n * 48 + V * (192 + 64 + 16) + (scene.n - V) * 16)
+        sort_bytes.append(K * (8 * 4 * 2 + 4) + K * 8)     # 4 passes r+w of key+val, histogram read, ranges
+    pre_gbs = float(np.sum(pre_bytes) / (stage[:, 0].sum() / 1e3) / 1e9)
+    sort_gbs = float(np.sum(sort_bytes) / (stage[:, 2].sum() / 1e3) / 1e9)
+
+    # ---- end to end through the C-ABI with host buffers
+    host = {name: getattr(ds, name).cpu().pin_memory() for name in
+            ("means", "log_scales", "quats", "opacity_logits", "sh", "vhat_train")}
+    h_rgb = torch.empty(3, H, W, pin_memory=True)
+    h_alpha = torch.empty(H, W, pin_memory=True)
+    h2d = sum(t.numel() * 4 for t in host.values())
+    d2h = (h_rgb.numel() + h_alpha.numel()) * 4
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(4, min(args.steps, 16))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(e2e_steps):
+        for name, t in host.items():
+            getattr(ds, name).copy_(t, non_blocking=True)
+        frame(k)
+        h_rgb.copy_(rgb, non_blocking=True)
+        h_alpha.copy_(alpha, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = e2e_steps / (e0.elapsed_time(e1) / 1e3) * world
+
+    launches_per_frame = 1 + 5 + 8 + 1   # preprocess; cull count+3 scan+emit; sort clip+init+hist+4 passes+ranges; render
+    mean = lambda key: float(np.mean([p[key] for p in per_pose]))
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "pair_capacity": args.capacity},
+        "stage_ms": {name: float(stage[:, j].mean()) for j, name in
+                     enumerate(("preprocess", "cull", "sort", "render"))},
+        "per_frame": {"visible": mean("n_visible"), "pairs": mean("n_pairs"),
+                      "evaluations": mean("evaluations"), "blended": mean("blended"),
+                      "misorders": mean("misorders"), "tiles_tested": mean("tiles_tested")},
+        "evals_per_s": float(np.sum(ev_by_step) / (total_ms / 1e3)),
+        "roofline": {"kernel": "render", "bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops, "traffic": None,
+                     "peak_source": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                     "ops_per_evaluation": OPS_PER_EVAL},
+        "hbm": {"preprocess_gbs": pre_gbs, "sort_gbs": sort_gbs, "peak_gbs": hbm_peak,
+                "peak_source": hbm_src, "preprocess_frac": pre_gbs / hbm_peak,
+                "sort_frac": sort_gbs / hbm_peak},
+        "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_frame * (args.steps + 0),
+        "clocks": clocks,
+        "wall_s_timed": wall,
+        "scene_generation_s": t_gen,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc, cores, frame_s = cpu_baseline(scene, poses, args.cpu_seconds, W * H)
+        line["cpu_baseline"] = {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * aaag.h -- C ABI of a GB300 (sm_103a) renderer for 3D-evaluated Gaussians
+ * with an adaptive 3D smoothing filter, view-space bounds, 3D frustum tile
+ * culling, per-pixel depth ordering and front-to-back compositing
+ * (AAA-Gaussians, arXiv 2504.12811).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All array pointers are DEVICE pointers owned by the caller unless a
+ *   comment says "host".  Arrays are dense, C-contiguous float32 / uint32.
+ * - Nothing here allocates device memory.  Per-frame storage lives in a
+ *   caller-provided workspace buffer (aaag_workspace_bytes / _init).
+ * - Calls are asynchronous and ordered on the given stream.  Host-side
+ *   argument errors return a status immediately and launch nothing.  Errors
+ *   only the device can see (pair capacity exceeded, a bounded wait that gave
+ *   up) set flags in the workspace that aaag_get_stats reports; the frame is
+ *   then invalid and no call traps, asserts or hangs.
+ * - A workspace is used by one stream at a time.
+ * - Images are planar: rgb[3][height][width], alpha[height][width]; pixel
+ *   (px, py) is sampled at its centre (px + 0.5, py + 0.5).
+ * - View space: x right, y down, z forward.  Pinhole cameras only (the
+ *   bounding is tied to the pinhole model, paper Sec. 5).
+ */
+#ifndef AAAG_H_
+#define AAAG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AAAG_OK = 0,
+  AAAG_ERR_INVALID_ARG = 1,  /* null pointer, bad size, non-finite camera     */
+  AAAG_ERR_CAPACITY = 2,     /* workspace too small (host check) or pair
+                                capacity exceeded on the device              */
+  AAAG_ERR_CUDA = 3,         /* a CUDA launch or copy failed                 */
+  AAAG_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up           */
+  AAAG_ERR_UNSUPPORTED = 5   /* e.g. SH degree > 3, image too large          */
+} aaag_status;
+
+/* Scene (paper Sec. 3.1: mean mu, scale s, rotation quaternion q, opacity;
+ * view-dependent colour as real spherical harmonics; Sec. 3.2: the training
+ * sampling frequency v_hat_train of the 3D smoothing filter).  Device
+ * pointers, caller-owned, read only:
+ *   means          [n][3]  world space
+ *   log_scales     [n][3]  s = exp(log_scales)
+ *   quats          [n][4]  (w, x, y, z), normalised inside
+ *   opacity_logits [n]     opacity = sigmoid(logit)
+ *   sh             [n][(sh_degree+1)^2][3]  coefficients, (l,m) order
+ *                  (0,0),(1,-1),(1,0),(1,1),(2,-2)...; real orthonormal SH
+ *                  with Condon-Shortley phase; colour = max(0, sum + 0.5)
+ *   vhat_train     [n]     pixels per world unit seen in training; +inf = none
+ */
+typedef struct {
+  int64_t n;
+  int32_t sh_degree;              /* 0..3 */
+  int32_t reserved;
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+  const float* vhat_train;
+} aaag_scene;
+
+/* Pinhole camera (paper Sec. 3.1 Eq. 4: view matrix V, projection P,
+ * viewport M_vp).  Host struct, copied at call time. */
+typedef struct {
+  float viewmat[16];   /* world -> view, row-major 4x4, last row (0,0,0,1)  */
+  float fx, fy;        /* focal lengths in pixels                           */
+  float cx, cy;        /* principal point in pixels                         */
+  int32_t width, height;
+  float znear;         /* near plane (Sec. 3.3); e.g. 0.2                   */
+  float bg[3];         /* background colour blended behind the last layer   */
+} aaag_camera;
+
+/* Method parameters. */
+#define AAAG_FLAG_NO_FILTER 1u  /* ablation: no 3D smoothing filter (phi=1)  */
+#define AAAG_FLAG_NO_CULL   2u  /* ablation: keep every tile of the bounds   */
+typedef struct {
+  float k;             /* filter size, Sec. 4: k = 0.3                       */
+  float eps;           /* angle clamp epsilon of Sec. 3.3 Eq. 17, e.g. 1e-3  */
+  uint32_t flags;      /* AAAG_FLAG_*                                        */
+  int32_t reserved;
+} aaag_params;
+
+typedef struct aaag_workspace aaag_workspace;
+
+/* Device-side frame statistics (aaag_get_stats). */
+typedef struct {
+  uint64_t n_gaussians;    /* n of the last preprocess                      */
+  uint64_t n_visible;      /* survived discard + whole-frustum cull         */
+  uint64_t n_pairs;        /* (tile, Gaussian) pairs kept by tile culling   */
+  uint64_t pair_capacity;
+  uint64_t tiles_tested;   /* tiles inside the bounds that were culled/kept */
+  uint64_t evaluations;    /* pixel x Gaussian evaluations in aaag_render   */
+  uint64_t blended;        /* contributors blended                          */
+  uint64_t misorders;      /* forced emissions of the per-pixel buffer      */
+  uint32_t capacity_overflow;  /* 1 when n_pairs > pair_capacity            */
+  uint32_t timeout;            /* 1 when a bounded device wait gave up       */
+} aaag_stats;
+
+/* Gradients, same layout as aaag_scene (device pointers, caller-owned,
+ * overwritten). */
+typedef struct {
+  float* means;
+  float* log_scales;
+  float* quats;
+  float* opacity_logits;
+  float* sh;
+} aaag_grads;
+
+/* Internal arrays of a workspace, for inspection by tests and tools.  Device
+ * pointers into the workspace buffer; valid until the next call that writes
+ * them. */
+typedef struct {
+  float* records;        /* [n][16]: rows t1,t2,t3 of T_view = V T (Gaussian
+                            space -> view space; t_i = (A_i0,A_i1,A_i2,mu_v,i)),
+                            then (r, g, b, o_hat)                            */
+  uint32_t* aux;         /* [n][4]: tile rect (tx0 | ty0<<16, tx1 | ty1<<16),
+                            tau_rho bits, depth-key bits; empty rect
+                            (tx0 > tx1) = not visible                         */
+  uint32_t* counts;      /* [n] chunks of 32 candidate tiles per Gaussian    */
+  uint32_t* offsets;     /* [n] exclusive prefix sum of counts               */
+  uint32_t* keys_unsorted;   /* [capacity] pair keys as emitted              */
+  uint32_t* vals_unsorted;   /* [capacity] Gaussian index per pair           */
+  uint32_t* keys_sorted;     /* [capacity] after aaag_sort                   */
+  uint32_t* vals_sorted;
+  uint32_t* tile_ranges; /* [tiles][2] start, end of each tile's pairs       */
+  float* final_T;        /* [height][width] transmittance after the last blend */
+  uint32_t* n_blended;   /* [height][width] contributors blended             */
+  int32_t tiles_x, tiles_y;
+  int32_t tile_bits;     /* key = tile << (32 - tile_bits) | depth key       */
+  int32_t depth_shift;   /* depth key = (bits(z) - bits(znear)) >> shift      */
+} aaag_workspace_view;
+
+/* --------------------------------------------------------------------------
+ * Workspace.  Bytes needed for n Gaussians, a width x height image and up to
+ * pair_capacity (tile, Gaussian) pairs.  The caller allocates that many bytes
+ * of device memory (256-byte aligned) and keeps them alive while the
+ * workspace is used; _init writes a small host-side descriptor to *ws
+ * (malloc'd; release with _destroy, which never frees dev_mem).
+ * Errors: INVALID_ARG (null, n < 0, size <= 0), CAPACITY (bytes too small),
+ * UNSUPPORTED (more than 2^16 tiles or pair_capacity >= 2^30).
+ * ------------------------------------------------------------------------ */
+size_t aaag_workspace_bytes(int64_t n, int32_t width, int32_t height,
+                            int64_t pair_capacity);
+aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n,
+                                int32_t width, int32_t height,
+                                int64_t pair_capacity, aaag_workspace** ws);
+void aaag_workspace_destroy(aaag_workspace* ws);
+aaag_status aaag_workspace_get_view(const aaag_workspace* ws,
+                                    aaag_workspace_view* out /* host */);
+
+/* --------------------------------------------------------------------------
+ * aaag_preprocess -- per-Gaussian preparation for one view (Sec. 3.2, 3.3,
+ * 3.4 last paragraph):
+ *   s = exp(log s), R(q/|q|), o = sigmoid(logit); view mean mu_v = V mu;
+ *   v_hat = fx / max(z_v, znear) (Eq. 6), v_hat' = min(v_hat_train, v_hat)
+ *   (Eq. 13); s_hat_i = s_i^2 + k / v_hat'^2; amplitude factor of Eq. 12;
+ *   o_hat = o * factor; tau_rho = 2 ln(255 o_hat) (alpha >= 1/255 inside);
+ *   discard when o_hat <= 1/255 or the camera is inside the tau-ellipsoid;
+ *   view-space angular bounds of Eq. 14-17 -> tile rectangle; cull against
+ *   the whole image frustum truncated at znear (Eq. 18 over the image);
+ *   SH colour; depth key from the front of the tau-ellipsoid.
+ * Reads scene arrays; writes the workspace records (n must equal the n the
+ * workspace was created for, width/height likewise).  Resets the frame
+ * statistics.
+ * Errors: INVALID_ARG, UNSUPPORTED (sh_degree > 3), CUDA.
+ * ------------------------------------------------------------------------ */
+aaag_status aaag_preprocess(const aaag_scene* scene /* host struct */,
+                            const aaag_camera* camera /* host */,
+                            const aaag_params* params /* host; NULL = defaults */,
+                            aaag_workspace* ws, cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
+ * aaag_cull -- 3D frustum tile culling (Sec. 3.4, Eq. 18, and the near-plane
+ * tile rule of Sec. 3.3): for every tile of a visible Gaussian's rectangle,
+ * keep the tile iff min over the tile's frustum (planes through the tile
+ * borders, truncated at znear) of rho^2 is below tau_rho; emit one
+ * (key, Gaussian index) pair per kept tile, key = tile id (high bits) and the
+ * quantised front depth (low bits).  Pairs beyond the capacity are dropped
+ * and flagged (aaag_get_stats -> capacity_overflow).
+ * Errors: INVALID_ARG, CUDA.
+ * ------------------------------------------------------------------------ */
+aaag_status aaag_cull(aaag_workspace* ws, cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
+ * aaag_sort -- global depth sort of the pairs (Sec. 3.1 'Blending Sort
+ * Order': tile-major, front depth minor) by a stable LSD radix sort with
+ * 8-bit digits and decoupled look-back (one pass per digit), then the
+ * [start, end) range of each tile.  The pair count is read on the device.
+ * Errors: CUDA; a look-back wait that gives up sets the timeout flag.
+ * ------------------------------------------------------------------------ */
+aaag_status aaag_sort(aaag_workspace* ws, cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
+ * aaag_render -- per-pixel 3D evaluation and compositing (Sec. 3.1 'Evaluation
+ * in 3D'): for each pixel and each pair of its tile, the Gaussian's maximum
+ * along the pixel ray rho^2 = |h1 n2 - h2 n1|^2 / |n1 x n2|^2 from the planes
+ * pi' = T'^T pi_x, T'^T pi_y (Eq. 4-5) and the depth t* of that maximum;
+ * alpha = min(0.99, o_hat exp(-rho^2/2)); contributors with alpha >= 1/255
+ * and t* >= znear are re-sorted per pixel by t* in a register buffer that
+ * releases an entry once every later pair of the tile is known to lie behind
+ * it (per-ray sorting, Sec. 4 'Implementation Details'); front-to-back
+ * blending stops before transmittance would fall below 1e-4.
+ * Writes rgb[3][H][W] = C + T * bg and alpha[H][W] = 1 - T (device,
+ * caller-owned), plus final T and blended counts in the workspace.
+ * Errors: INVALID_ARG (null outputs), CUDA.
+ * ------------------------------------------------------------------------ */
+aaag_status aaag_render(aaag_workspace* ws, float* rgb, float* alpha,
+                        cudaStream_t stream);
+
+/* Convenience: preprocess + cull + sort + render in one call. */
+aaag_status aaag_render_frame(const aaag_scene* scene, const aaag_camera* camera,
+                              const aaag_params* params, aaag_workspace* ws,
+                              float* rgb, float* alpha, cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
+ * aaag_radix_sort -- the stable LSD radix sort used by aaag_sort, on caller
+ * arrays: sorts keys[0..n) (low `key_bits` bits significant, 1..32) and
+ * carries vals along.  keys_alt / vals_alt are ping-pong buffers of n
+ * elements; scratch is aaag_radix_sort_scratch_bytes(n) bytes.  The result
+ * ends in (keys, vals) when the number of 8-bit passes is even, else in
+ * (keys_alt, vals_alt); *result_in_alt (host) says which.  n is a host
+ * value here.  Errors: INVALID_ARG, CAPACITY (scratch too small), CUDA.
+ * ------------------------------------------------------------------------ */
+size_t aaag_radix_sort_scratch_bytes(int64_t n);
+aaag_status aaag_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                            uint32_t* vals_alt, int64_t n, int32_t key_bits,
+                            void* scratch, size_t scratch_bytes,
+                            int32_t* result_in_alt, cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
+ * aaag_get_stats -- synchronises `stream` and copies the frame statistics to
+ * *out (host).  Returns CAPACITY if the pair capacity overflowed, TIMEOUT if a
+ * bounded device wait gave up, else OK.
+ * ------------------------------------------------------------------------ */
+aaag_status aaag_get_stats(aaag_workspace* ws, aaag_stats* out, cudaStream_t stream);
+
+/* Text of the last host-side error on this thread (static storage). */
+const char* aaag_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AAAG_H_ */

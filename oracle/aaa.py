@@ -531,19 +531,23 @@ def tile_min_rho2(prep, gauss_idx, tile_x, tile_y, near: bool = True):
 # pixels where float32 rounding can legitimately flip a discrete decision
 # ---------------------------------------------------------------------------
 
-def ambiguous_pixels(prep, px, py, rel_alpha=2e-3, rel_t=1e-4, rel_tau=1e-3):
+def ambiguous_pixels(prep, px, py, rel_alpha=2e-5, rel_t=2e-6, rel_tau=1e-4, swap=2e-4):
     """Pixels whose result depends on a decision that float32 evaluation may
-    take differently from float64 (not a definition of the method; used to
-    exclude those pixels from the strict max-abs comparison):
-      alpha within rel_alpha of 1/255; t* within rel_t of z_near; two
-      blended contributors whose t* differ by less than rel_t; a Gaussian
-      whose camera-inside test or o_hat > 1/255 test is within rel_tau of its
-      threshold."""
+    take differently from float64 (test tolerance logic, not part of the
+    method):
+      * an alpha within rel_alpha (relative) of 1/255;
+      * a depth t* within rel_t (relative) of z_near for a contributor;
+      * a Gaussian whose camera-inside test or o_hat > 1/255 test is within
+        rel_tau of its threshold, touching the pixel;
+      * two depth-adjacent contributors whose t* differ by less than rel_t
+        (relative) and whose swap would change the pixel by more than `swap`
+        (swapping a before b changes C by T_a alpha_a alpha_b (c_a - c_b))."""
     rho2, tstar = ray_maximum(prep, px, py)
     raw = prep["o_hat"].unsqueeze(0) * torch.exp(-0.5 * rho2)
     view = prep["view"]
     live = prep["alive"].unsqueeze(0)
     near_alpha = (raw - ALPHA_MIN).abs() < rel_alpha * ALPHA_MIN
+    contrib = live & (raw >= ALPHA_MIN) & (tstar >= view.znear)
     near_z = ((tstar - view.znear).abs() < rel_t * view.znear) & (raw >= ALPHA_MIN * (1 - rel_alpha))
     uu = (prep["u_cam"] ** 2).sum(-1)
     edge_g = ((uu - prep["tau"]).abs() < rel_tau * prep["tau"].abs()) | \
@@ -551,10 +555,21 @@ def ambiguous_pixels(prep, px, py, rel_alpha=2e-3, rel_t=1e-4, rel_tau=1e-3):
     touched = raw >= ALPHA_MIN * (1 - rel_alpha)
     flag = ((near_alpha | near_z) & (live | edge_g.unsqueeze(0))).any(1)
     flag |= (touched & edge_g.unsqueeze(0)).any(1)
-    contrib = live & (raw >= ALPHA_MIN) & (tstar >= view.znear)
+    # order ties that matter
     key = torch.where(contrib, tstar, torch.full_like(tstar, math.inf))
-    srt = torch.sort(key, 1).values
-    fin = torch.isfinite(srt[:, 1:]) & torch.isfinite(srt[:, :-1])
-    close = fin & ((srt[:, 1:] - srt[:, :-1]) <= rel_t * srt[:, :-1].abs())
-    flag |= close.any(1)
+    srt = torch.sort(key, dim=1, stable=True)
+    m = int(contrib.sum(1).max().item()) if contrib.numel() else 0
+    if m >= 2:
+        order = srt.indices[:, :m]
+        t_s = srt.values[:, :m]
+        a_s = torch.clamp(torch.gather(raw, 1, order), max=ALPHA_MAX)
+        valid = torch.isfinite(t_s)
+        a_s = torch.where(valid, a_s, torch.zeros_like(a_s))
+        T_b = torch.cumprod(torch.cat([torch.ones_like(a_s[:, :1]), 1 - a_s[:, :-1]], 1), 1)
+        c_s = prep["rgb"][order]                                   # [P,m,3]
+        close = valid[:, 1:] & valid[:, :-1] & \
+            ((t_s[:, 1:] - t_s[:, :-1]) <= rel_t * t_s[:, :-1].abs())
+        effect = T_b[:, :-1] * a_s[:, :-1] * a_s[:, 1:] * \
+            (c_s[:, :-1, :] - c_s[:, 1:, :]).abs().amax(-1)
+        flag |= (close & (effect > swap)).any(1)
     return flag

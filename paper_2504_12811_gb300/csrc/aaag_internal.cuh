@@ -1,0 +1,145 @@
+// Internal definitions shared by the CUDA translation units of libaaag.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "aaag.h"
+
+namespace aaag {
+
+constexpr int kTile = 16;                 // 16x16 pixel tiles
+constexpr int kTilePixels = kTile * kTile;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTStop = 1e-4f;
+constexpr int kMaxShDegree = 3;
+constexpr int kSortItems = 16;            // keys per thread in a sort pass
+constexpr int kSortThreads = 256;
+constexpr int kSortTileKeys = kSortItems * kSortThreads;   // 4096
+constexpr int kMaxTileBits = 16;          // at most 65536 tiles per image
+
+// Frame constants, prepared on the host in double precision and rounded once.
+struct FrameConst {
+  float Rv[9];          // world -> view rotation (row-major)
+  float tv[3];          // world -> view translation
+  float o[3];           // camera origin in world space: -Rv^-1 tv
+  float fx, fy, cx, cy;
+  int W, H, tiles_x, tiles_y;
+  float znear;
+  float bg[3];
+  float k;              // filter size
+  float eps;            // angle clamp epsilon
+  uint32_t flags;
+  int tile_bits;        // bits of the tile id in a pair key
+  int depth_bits;       // 32 - tile_bits
+  int depth_shift;      // depth key = (bits(z) - bits(znear)) >> depth_shift
+  uint32_t znear_bits;
+  int sh_degree;
+};
+
+struct SceneDev {
+  int64_t n;
+  int sh_degree;
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+  const float* vhat_train;
+};
+
+// Per-Gaussian record (64 B): rows of T_view = V T (Gaussian space -> view
+// space, T = [R S' mu; 0 1], S' = diag(sqrt(s_hat))) and (r, g, b, o_hat).
+struct __align__(16) Record {
+  float4 t1, t2, t3;
+  float4 rgba;
+};
+
+// Stats slots in the workspace (uint64 each).
+enum StatSlot : int {
+  kStatVisible = 0,
+  kStatPairs = 1,
+  kStatTilesTested = 2,
+  kStatEvaluations = 3,
+  kStatBlended = 4,
+  kStatMisorders = 5,
+  kStatOverflow = 6,
+  kStatTimeout = 7,
+  kStatSortEpoch = 8,
+  kStatChunks = 9,         // chunks of 32 candidate tiles (K2 work items)
+  kStatChunksClipped = 14, // uint32: chunk count clipped to the chunk capacity
+  kStatPairsClipped = 15,  // uint32: pair count clipped to the pair capacity
+  kStatCount = 16
+};
+
+}  // namespace aaag
+
+// Host-side workspace descriptor.
+struct aaag_workspace {
+  int64_t n;
+  int width, height, tiles_x, tiles_y, n_tiles;
+  int64_t capacity;
+  size_t bytes;
+  char* base;
+  aaag::Record* records;
+  uint4* aux;
+  uint32_t* counts;              // [n] chunks of 32 candidate tiles per Gaussian
+  uint32_t* offsets;             // [n] exclusive prefix of counts
+  int64_t chunk_capacity;
+  uint32_t* chunk_owner;         // [chunk_capacity] Gaussian of each chunk
+  uint32_t* chunk_mask;          // [chunk_capacity] kept-tile ballot of each chunk
+  uint32_t* chunk_pair_offsets;  // [chunk_capacity] first pair of each chunk
+  unsigned long long* scan_partials;   // per scan block
+  uint32_t* keys[2];
+  uint32_t* vals[2];
+  uint32_t* sort_hist;           // [4][256]
+  uint32_t* sort_counters;       // [4] tile counters per pass
+  unsigned long long* sort_lookback;   // [max sort tiles][256]
+  uint2* ranges;                 // [n_tiles]
+  float* final_T;                // [H*W]
+  uint32_t* n_blended;           // [H*W]
+  unsigned long long* stats;     // [kStatCount]
+  aaag::FrameConst fc;
+  bool have_frame;
+  int sorted_in_alt;             // which buffer holds the sorted pairs
+  int64_t n_scan_blocks;
+  int64_t n_sort_tiles;
+};
+
+namespace aaag {
+
+// ---------------------------------------------------------------------------
+// host helpers (api.cu)
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+aaag_status check_launch(const char* what);
+
+// kernel launchers (one per translation unit)
+aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_t st);
+aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st);
+aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st);
+aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st);
+aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                                uint32_t* vals_alt, const uint32_t* n_dev, int64_t n_max,
+                                int key_bits, uint32_t* hist, uint32_t* counters,
+                                unsigned long long* lookback, unsigned long long* epoch,
+                                unsigned long long* timeout_flag, int* result_in_alt,
+                                cudaStream_t st);
+size_t radix_sort_scratch(int64_t n_max);
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 xyz(float4 a) { return f3(a.x, a.y, a.z); }
+
+}  // namespace aaag

@@ -1,0 +1,415 @@
+// C ABI of libaaag: workspace management, argument checks, host-side frame
+// setup and the entry points declared in include/aaag.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+
+#include "aaag_internal.cuh"
+
+namespace aaag {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+aaag_status check_launch(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return AAAG_ERR_CUDA;
+  }
+  return AAAG_OK;
+}
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct Layout {
+  size_t records, aux, counts, offsets, partials, owner, mask, pofs, keys0, keys1, vals0, vals1, hist, counters,
+      lookback, ranges, final_T, n_blended, stats, total;
+};
+
+int tiles_of(int size) { return (size + kTile - 1) / kTile; }
+
+// Work items of the tile culling: every visible Gaussian has at least one
+// chunk of 32 candidate tiles; the pair capacity bounds the rest.
+int64_t chunk_capacity_of(int64_t n, int64_t cap) { return n + cap / 4 + 1024; }
+
+Layout layout_of(int64_t n, int w, int h, int64_t cap) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + (bytes ? bytes : 1));
+    return at;
+  };
+  const int64_t ccap = chunk_capacity_of(n, cap);
+  const int64_t nsb = (std::max(n, ccap) + 4095) / 4096 + 1;
+  const int64_t nst = (cap + kSortTileKeys - 1) / kSortTileKeys + 1;
+  const size_t ntiles = (size_t)tiles_of(w) * tiles_of(h);
+  L.records = take((size_t)n * sizeof(Record));
+  L.aux = take((size_t)n * 16);
+  L.counts = take((size_t)n * 4);
+  L.offsets = take((size_t)n * 4);
+  L.partials = take((size_t)nsb * 8);
+  L.owner = take((size_t)ccap * 4);
+  L.mask = take((size_t)ccap * 4);
+  L.pofs = take((size_t)ccap * 4);
+  L.keys0 = take((size_t)cap * 4);
+  L.keys1 = take((size_t)cap * 4);
+  L.vals0 = take((size_t)cap * 4);
+  L.vals1 = take((size_t)cap * 4);
+  L.hist = take(4 * 256 * 4);
+  L.counters = take(4 * 4);
+  L.lookback = take((size_t)nst * 256 * 8);
+  L.ranges = take(ntiles * sizeof(uint2));
+  L.final_T = take((size_t)w * h * 4);
+  L.n_blended = take((size_t)w * h * 4);
+  L.stats = take(kStatCount * 8);
+  L.total = off;
+  return L;
+}
+
+bool finite_camera(const aaag_camera* c) {
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(c->viewmat[i])) return false;
+  const float v[] = {c->fx, c->fy, c->cx, c->cy, c->znear, c->bg[0], c->bg[1], c->bg[2]};
+  for (float x : v)
+    if (!std::isfinite(x)) return false;
+  return c->fx > 0 && c->fy > 0 && c->znear > 0;
+}
+
+// Frame constants in double precision: exact inverse of the view rotation for
+// the camera origin, tile and key geometry.
+aaag_status make_frame(const aaag_camera* cam, const aaag_params* prm, int sh_degree,
+                       const aaag_workspace* ws, FrameConst* fc) {
+  const float* V = cam->viewmat;
+  double R[9], t[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) R[3 * r + c] = V[4 * r + c];
+    t[r] = V[4 * r + 3];
+  }
+  const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                     R[2] * (R[3] * R[7] - R[4] * R[6]);
+  if (!(std::fabs(det) > 1e-12)) {
+    set_error("view matrix rotation is singular");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  double Ri[9];
+  Ri[0] = (R[4] * R[8] - R[5] * R[7]) / det;
+  Ri[1] = (R[2] * R[7] - R[1] * R[8]) / det;
+  Ri[2] = (R[1] * R[5] - R[2] * R[4]) / det;
+  Ri[3] = (R[5] * R[6] - R[3] * R[8]) / det;
+  Ri[4] = (R[0] * R[8] - R[2] * R[6]) / det;
+  Ri[5] = (R[2] * R[3] - R[0] * R[5]) / det;
+  Ri[6] = (R[3] * R[7] - R[4] * R[6]) / det;
+  Ri[7] = (R[1] * R[6] - R[0] * R[7]) / det;
+  Ri[8] = (R[0] * R[4] - R[1] * R[3]) / det;
+  for (int i = 0; i < 9; ++i) fc->Rv[i] = (float)R[i];
+  for (int i = 0; i < 3; ++i) {
+    fc->tv[i] = (float)t[i];
+    fc->o[i] = (float)-(Ri[3 * i] * t[0] + Ri[3 * i + 1] * t[1] + Ri[3 * i + 2] * t[2]);
+    fc->bg[i] = cam->bg[i];
+  }
+  fc->fx = cam->fx;
+  fc->fy = cam->fy;
+  fc->cx = cam->cx;
+  fc->cy = cam->cy;
+  fc->W = cam->width;
+  fc->H = cam->height;
+  fc->tiles_x = ws->tiles_x;
+  fc->tiles_y = ws->tiles_y;
+  fc->znear = cam->znear;
+  fc->k = prm ? prm->k : 0.3f;
+  fc->eps = prm ? prm->eps : 1e-3f;
+  fc->flags = prm ? prm->flags : 0u;
+  int bits = 1;
+  while ((1 << bits) < ws->n_tiles) ++bits;
+  fc->tile_bits = bits;
+  fc->depth_bits = 32 - bits;
+  // (bits(z) - bits(znear)) spans < 2^28 for z/znear below 2^24
+  fc->depth_shift = fc->depth_bits >= 28 ? 0 : 28 - fc->depth_bits;
+  uint32_t zb;
+  std::memcpy(&zb, &cam->znear, 4);
+  fc->znear_bits = zb;
+  fc->sh_degree = sh_degree;
+  return AAAG_OK;
+}
+
+__global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
+
+}  // namespace
+}  // namespace aaag
+
+using namespace aaag;
+
+extern "C" {
+
+const char* aaag_last_error(void) { return g_err; }
+
+size_t aaag_workspace_bytes(int64_t n, int32_t width, int32_t height, int64_t pair_capacity) {
+  if (n < 0 || width <= 0 || height <= 0 || pair_capacity < 0) return 0;
+  return layout_of(n, width, height, pair_capacity).total;
+}
+
+aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t width, int32_t height,
+                                int64_t pair_capacity, aaag_workspace** ws) {
+  if (!dev_mem || !ws || n < 0 || n >= (1ll << 32) || width <= 0 || height <= 0 || pair_capacity < 0) {
+    set_error("aaag_workspace_init: invalid argument");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (((uintptr_t)dev_mem) % kAlign) {
+    set_error("aaag_workspace_init: device memory must be %zu-byte aligned", kAlign);
+    return AAAG_ERR_INVALID_ARG;
+  }
+  const int tx = tiles_of(width), ty = tiles_of(height);
+  if ((int64_t)tx * ty > (1 << kMaxTileBits) || pair_capacity >= (1ll << 30)) {
+    set_error("aaag_workspace_init: at most 65536 tiles and 2^30 pairs");
+    return AAAG_ERR_UNSUPPORTED;
+  }
+  const Layout L = layout_of(n, width, height, pair_capacity);
+  if (bytes < L.total) {
+    set_error("aaag_workspace_init: %zu bytes given, %zu needed", bytes, L.total);
+    return AAAG_ERR_CAPACITY;
+  }
+  auto* w = static_cast<aaag_workspace*>(std::calloc(1, sizeof(aaag_workspace)));
+  if (!w) {
+    set_error("aaag_workspace_init: out of host memory");
+    return AAAG_ERR_CAPACITY;
+  }
+  char* b = static_cast<char*>(dev_mem);
+  w->n = n;
+  w->width = width;
+  w->height = height;
+  w->tiles_x = tx;
+  w->tiles_y = ty;
+  w->n_tiles = tx * ty;
+  w->capacity = pair_capacity;
+  w->bytes = bytes;
+  w->base = b;
+  w->records = reinterpret_cast<Record*>(b + L.records);
+  w->aux = reinterpret_cast<uint4*>(b + L.aux);
+  w->counts = reinterpret_cast<uint32_t*>(b + L.counts);
+  w->offsets = reinterpret_cast<uint32_t*>(b + L.offsets);
+  w->scan_partials = reinterpret_cast<unsigned long long*>(b + L.partials);
+  w->chunk_capacity = chunk_capacity_of(n, pair_capacity);
+  w->chunk_owner = reinterpret_cast<uint32_t*>(b + L.owner);
+  w->chunk_mask = reinterpret_cast<uint32_t*>(b + L.mask);
+  w->chunk_pair_offsets = reinterpret_cast<uint32_t*>(b + L.pofs);
+  w->keys[0] = reinterpret_cast<uint32_t*>(b + L.keys0);
+  w->keys[1] = reinterpret_cast<uint32_t*>(b + L.keys1);
+  w->vals[0] = reinterpret_cast<uint32_t*>(b + L.vals0);
+  w->vals[1] = reinterpret_cast<uint32_t*>(b + L.vals1);
+  w->sort_hist = reinterpret_cast<uint32_t*>(b + L.hist);
+  w->sort_counters = reinterpret_cast<uint32_t*>(b + L.counters);
+  w->sort_lookback = reinterpret_cast<unsigned long long*>(b + L.lookback);
+  w->ranges = reinterpret_cast<uint2*>(b + L.ranges);
+  w->final_T = reinterpret_cast<float*>(b + L.final_T);
+  w->n_blended = reinterpret_cast<uint32_t*>(b + L.n_blended);
+  w->stats = reinterpret_cast<unsigned long long*>(b + L.stats);
+  w->n_scan_blocks = (n + 4095) / 4096;
+  w->n_sort_tiles = (pair_capacity + kSortTileKeys - 1) / kSortTileKeys;
+  // the look-back epoch lives in the stats block and must start defined; the
+  // look-back words are cleared once so that no stale word can match an epoch
+  if (cudaMemset(w->stats, 0, kStatCount * 8) != cudaSuccess ||
+      cudaMemset(w->sort_lookback, 0, (size_t)(w->n_sort_tiles + 1) * 256 * 8) != cudaSuccess) {
+    std::free(w);
+    return check_launch("workspace_init memset");
+  }
+  *ws = w;
+  return AAAG_OK;
+}
+
+void aaag_workspace_destroy(aaag_workspace* ws) { std::free(ws); }
+
+aaag_status aaag_workspace_get_view(const aaag_workspace* ws, aaag_workspace_view* out) {
+  if (!ws || !out) {
+    set_error("aaag_workspace_get_view: null argument");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->records = reinterpret_cast<float*>(ws->records);
+  out->aux = reinterpret_cast<uint32_t*>(ws->aux);
+  out->counts = ws->counts;
+  out->offsets = ws->offsets;
+  out->keys_unsorted = ws->keys[0];
+  out->vals_unsorted = ws->vals[0];
+  out->keys_sorted = ws->keys[ws->sorted_in_alt];
+  out->vals_sorted = ws->vals[ws->sorted_in_alt];
+  out->tile_ranges = reinterpret_cast<uint32_t*>(ws->ranges);
+  out->final_T = ws->final_T;
+  out->n_blended = ws->n_blended;
+  out->tiles_x = ws->tiles_x;
+  out->tiles_y = ws->tiles_y;
+  out->tile_bits = ws->have_frame ? ws->fc.tile_bits : 0;
+  out->depth_shift = ws->have_frame ? ws->fc.depth_shift : 0;
+  return AAAG_OK;
+}
+
+aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, const aaag_params* params,
+                            aaag_workspace* ws, cudaStream_t stream) {
+  if (!scene || !camera || !ws) {
+    set_error("aaag_preprocess: null argument");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (scene->n != ws->n || camera->width != ws->width || camera->height != ws->height) {
+    set_error("aaag_preprocess: scene/camera size (%lld, %dx%d) differs from the workspace (%lld, %dx%d)",
+              (long long)scene->n, camera->width, camera->height, (long long)ws->n, ws->width, ws->height);
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (scene->sh_degree < 0 || scene->sh_degree > kMaxShDegree) {
+    set_error("aaag_preprocess: sh_degree %d not in 0..3", scene->sh_degree);
+    return AAAG_ERR_UNSUPPORTED;
+  }
+  if (scene->n > 0 && (!scene->means || !scene->log_scales || !scene->quats || !scene->opacity_logits ||
+                       !scene->sh || !scene->vhat_train)) {
+    set_error("aaag_preprocess: null scene array");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (((uintptr_t)scene->quats) % 16 || ((uintptr_t)scene->sh) % 16) {
+    set_error("aaag_preprocess: quats and sh must be 16-byte aligned");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (!finite_camera(camera)) {
+    set_error("aaag_preprocess: camera has non-finite or non-positive fields");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (params && (!(params->k >= 0.0f) || !(params->eps > 0.0f) || !(params->eps < 1.0f))) {
+    set_error("aaag_preprocess: params out of range");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  FrameConst fc;
+  std::memset(&fc, 0, sizeof(fc));
+  aaag_status e = make_frame(camera, params, scene->sh_degree, ws, &fc);
+  if (e != AAAG_OK) return e;
+  ws->fc = fc;
+  ws->have_frame = true;
+  ws->sorted_in_alt = 0;
+  // reset per-frame statistics (keep the sort epoch)
+  if (cudaMemsetAsync(ws->stats, 0, kStatSortEpoch * 8, stream) != cudaSuccess)
+    return check_launch("preprocess memset");
+  SceneDev s;
+  s.n = scene->n;
+  s.sh_degree = scene->sh_degree;
+  s.means = scene->means;
+  s.log_scales = scene->log_scales;
+  s.quats = scene->quats;
+  s.opacity_logits = scene->opacity_logits;
+  s.sh = scene->sh;
+  s.vhat_train = scene->vhat_train;
+  return launch_preprocess(s, ws, stream);
+}
+
+aaag_status aaag_cull(aaag_workspace* ws, cudaStream_t stream) {
+  if (!ws || !ws->have_frame) {
+    set_error("aaag_cull: workspace without a preprocessed frame");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  return launch_cull(ws, stream);
+}
+
+aaag_status aaag_sort(aaag_workspace* ws, cudaStream_t stream) {
+  if (!ws || !ws->have_frame) {
+    set_error("aaag_sort: workspace without a preprocessed frame");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  return launch_sort_pairs(ws, stream);
+}
+
+aaag_status aaag_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t stream) {
+  if (!ws || !ws->have_frame || !rgb || !alpha) {
+    set_error("aaag_render: null argument or no preprocessed frame");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  return launch_render(ws, rgb, alpha, stream);
+}
+
+aaag_status aaag_render_frame(const aaag_scene* scene, const aaag_camera* camera, const aaag_params* params,
+                              aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t stream) {
+  aaag_status e = aaag_preprocess(scene, camera, params, ws, stream);
+  if (e == AAAG_OK) e = aaag_cull(ws, stream);
+  if (e == AAAG_OK) e = aaag_sort(ws, stream);
+  if (e == AAAG_OK) e = aaag_render(ws, rgb, alpha, stream);
+  return e;
+}
+
+size_t aaag_radix_sort_scratch_bytes(int64_t n) { return n < 0 ? 0 : radix_sort_scratch(n); }
+
+aaag_status aaag_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                            int32_t key_bits, void* scratch, size_t scratch_bytes, int32_t* result_in_alt,
+                            cudaStream_t stream) {
+  if (n < 0 || n >= (1ll << 30) || key_bits < 1 || key_bits > 32 || !result_in_alt) {
+    set_error("aaag_radix_sort: invalid argument");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (n > 0 && (!keys || !vals || !keys_alt || !vals_alt || !scratch)) {
+    set_error("aaag_radix_sort: null pointer");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (n == 0) {
+    *result_in_alt = 0;
+    return AAAG_OK;
+  }
+  if (scratch_bytes < radix_sort_scratch(n) || ((uintptr_t)scratch) % 16) {
+    set_error("aaag_radix_sort: scratch too small or unaligned (%zu < %zu)", scratch_bytes,
+              radix_sort_scratch(n));
+    return AAAG_ERR_CAPACITY;
+  }
+  // scratch layout: hist | counters | epoch | timeout | n | lookback
+  char* b = static_cast<char*>(scratch);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(b);
+  uint32_t* counters = reinterpret_cast<uint32_t*>(b + 4096);
+  unsigned long long* epoch = reinterpret_cast<unsigned long long*>(b + 4096 + 64);
+  unsigned long long* timeout = epoch + 1;
+  uint32_t* n_dev = reinterpret_cast<uint32_t*>(epoch + 2);
+  unsigned long long* lookback = reinterpret_cast<unsigned long long*>(b + 4096 + 256);
+  set_u32_kernel<<<1, 1, 0, stream>>>(n_dev, (uint32_t)n);
+  int alt = 0;
+  const aaag_status e = radix_sort_device_n(keys, vals, keys_alt, vals_alt, n_dev, n, key_bits, hist, counters,
+                                            lookback, epoch, timeout, &alt, stream);
+  *result_in_alt = alt;
+  return e;
+}
+
+aaag_status aaag_get_stats(aaag_workspace* ws, aaag_stats* out, cudaStream_t stream) {
+  if (!ws || !out) {
+    set_error("aaag_get_stats: null argument");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  unsigned long long h[kStatCount];
+  if (cudaMemcpyAsync(h, ws->stats, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return check_launch("get_stats");
+  std::memset(out, 0, sizeof(*out));
+  out->n_gaussians = (uint64_t)ws->n;
+  out->n_visible = h[kStatVisible];
+  out->n_pairs = h[kStatPairs];
+  out->pair_capacity = (uint64_t)ws->capacity;
+  out->tiles_tested = h[kStatTilesTested];
+  out->evaluations = h[kStatEvaluations];
+  out->blended = h[kStatBlended];
+  out->misorders = h[kStatMisorders];
+  out->capacity_overflow = (uint32_t)h[kStatOverflow];
+  out->timeout = (uint32_t)h[kStatTimeout];
+  if (out->capacity_overflow) {
+    set_error("pair capacity %lld exceeded: %llu pairs", (long long)ws->capacity, (unsigned long long)h[kStatPairs]);
+    return AAAG_ERR_CAPACITY;
+  }
+  if (out->timeout) {
+    set_error("a bounded device wait gave up");
+    return AAAG_ERR_TIMEOUT;
+  }
+  return AAAG_OK;
+}
+
+}  // extern "C"

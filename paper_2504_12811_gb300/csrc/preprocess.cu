@@ -1,0 +1,282 @@
+// K1: per-Gaussian preprocessing for one view (paper Sec. 3.2-3.4).
+//
+// One thread per Gaussian; reads the scene arrays once (colour coefficients
+// only for Gaussians that survive), writes a 64-byte record and a 16-byte aux
+// word per visible Gaussian.  Memory-bound by design: everything else is a few
+// hundred FP32 operations per Gaussian.
+#include <cmath>
+
+#include "aaag_internal.cuh"
+#include "geometry.cuh"
+
+namespace aaag {
+namespace {
+
+constexpr float kPi = 3.14159265358979f;
+
+// Real SH (orthonormal, Condon-Shortley phase) expanded as polynomials in the
+// unit direction (x, y, z).  Constants are the normalisations
+// K_l^m * sqrt(2) (m != 0) of the associated-Legendre definition:
+//   1/(2 sqrt(pi)); sqrt(3/(4 pi));
+//   sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4;
+//   sqrt(35/(2 pi))/4, sqrt(105/pi)/2, sqrt(21/(2 pi))/4, sqrt(7/pi)/4,
+//   sqrt(105/pi)/4.
+constexpr float kY00 = 0.28209479177387814f;
+constexpr float kY1 = 0.4886025119029199f;
+constexpr float kY2a = 1.0925484305920792f;
+constexpr float kY2b = 0.31539156525252005f;
+constexpr float kY2c = 0.5462742152960396f;
+constexpr float kY3a = 0.5900435899266435f;
+constexpr float kY3b = 2.890611442640554f;
+constexpr float kY3c = 0.4570457994644658f;
+constexpr float kY3d = 0.3731763325901154f;
+constexpr float kY3e = 1.445305721320277f;
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, int deg, float* Y) {
+  Y[0] = kY00;
+  if (deg < 1) return;
+  Y[1] = -kY1 * y;
+  Y[2] = kY1 * z;
+  Y[3] = -kY1 * x;
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kY2a * x * y;
+  Y[5] = -kY2a * y * z;
+  Y[6] = kY2b * (2.0f * zz - xx - yy);
+  Y[7] = -kY2a * x * z;
+  Y[8] = kY2c * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = -kY3a * y * (3.0f * xx - yy);
+  Y[10] = kY3b * x * y * z;
+  Y[11] = -kY3c * y * (4.0f * zz - xx - yy);
+  Y[12] = kY3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+  Y[13] = -kY3c * x * (4.0f * zz - xx - yy);
+  Y[14] = kY3e * z * (xx - yy);
+  Y[15] = -kY3a * x * (xx - 3.0f * yy);
+}
+
+// Screen interval of one axis from the view-space tangent planes (Sec. 3.3,
+// Eq. 14-17).  Ai: row i of A = Rv R S' (view axis i of the Gaussian frame),
+// A3: the z row; mi, mz: view-space mean.  Returns false when the interval is
+// empty (the Gaussian lies behind the camera on this axis).
+__device__ __forceinline__ bool axis_bounds(float3 Ai, float3 A3, float mi, float mz, float tau,
+                                            float f, float c, float eps, float& p1, float& p2) {
+  const float sii = tau * dot3(Ai, Ai) - mi * mi;
+  const float si3 = tau * dot3(Ai, A3) - mi * mz;
+  const float S33 = tau * dot3(A3, A3);
+  const float s33 = S33 - mz * mz;
+  // s13^2 - s11 s33 without the mu^4 cancellation:
+  //   tau * (|Ai mz - A3 mi|^2 - tau |Ai x A3|^2)
+  const float3 w = mz * Ai - mi * A3;
+  const float3 cr = cross3(Ai, A3);
+  const float D = tau * (dot3(w, w) - tau * dot3(cr, cr));
+  const float lim = 0.5f * kPi - eps;
+  float a1 = -lim, a2 = lim;
+  const bool degenerate = !(D >= 0.0f) || fabsf(s33) <= 1e-5f * (S33 + mz * mz);
+  if (!degenerate) {
+    // roots of s33 tan^2 - 2 s13 tan + s11 = 0, numerically stable form
+    const float sq = sqrtf(D);
+    const float q = si3 + copysignf(sq, si3);
+    if (q != 0.0f) {
+      const float ra = atanf(q / s33);
+      const float rb = atanf(sii / q);
+      const float amu = atan2f(mi, mz);
+      // representative of a root angle in (amu - pi, amu]
+      auto lo = [&](float r) {
+        const float dlt = amu - r;
+        return amu - (dlt - kPi * floorf(dlt / kPi));
+      };
+      float b1 = lo(ra), b2 = lo(rb) + kPi;
+      if (b2 - b1 >= kPi) {
+        b1 = lo(rb);
+        b2 = lo(ra) + kPi;
+      }
+      a1 = fmaxf(-lim, b1);
+      a2 = fminf(lim, b2);
+      if (a1 > a2) return false;
+    }
+  }
+  p1 = f * tanf(a1) + c;
+  p2 = f * tanf(a2) + c;
+  // margin for float32 rounding of the angles
+  p1 -= 0.01f + 1e-5f * fabsf(p1);
+  p2 += 0.01f + 1e-5f * fabsf(p2);
+  return true;
+}
+
+__device__ __forceinline__ bool tile_range(float p1, float p2, int size, int ntiles, int& t0, int& t1) {
+  if (!(p2 >= 0.0f) || !(p1 <= (float)size)) return false;
+  p1 = fmaxf(p1, 0.0f);
+  p2 = fminf(p2, (float)size);
+  t0 = (int)floorf(p1 * (1.0f / kTile));
+  t1 = min((int)floorf(p2 * (1.0f / kTile)), ntiles - 1);
+  return t0 <= t1;
+}
+
+__global__ void __launch_bounds__(256)
+preprocess_kernel(SceneDev s, FrameConst fc, Record* __restrict__ rec, uint4* __restrict__ aux,
+                  uint32_t* __restrict__ chunks, unsigned long long* __restrict__ stats) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool visible = false;
+  if (i < s.n) {
+    const float mx = s.means[3 * i + 0], my = s.means[3 * i + 1], mz = s.means[3 * i + 2];
+    const float lx = s.log_scales[3 * i + 0], ly = s.log_scales[3 * i + 1],
+                lz = s.log_scales[3 * i + 2];
+    const float4 q4 = reinterpret_cast<const float4*>(s.quats)[i];
+    const float logit = s.opacity_logits[i];
+    const float vtrain = s.vhat_train[i];
+
+    // view-space mean
+    const float vx = fc.Rv[0] * mx + fc.Rv[1] * my + fc.Rv[2] * mz + fc.tv[0];
+    const float vy = fc.Rv[3] * mx + fc.Rv[4] * my + fc.Rv[5] * mz + fc.tv[1];
+    const float vz = fc.Rv[6] * mx + fc.Rv[7] * my + fc.Rv[8] * mz + fc.tv[2];
+
+    // activations (Sec. 3.1)
+    const float sx = expf(lx), sy = expf(ly), sz = expf(lz);
+    float qn = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+    const float qi = qn > 0.0f ? rsqrtf(qn) : 0.0f;
+    const float w = qn > 0.0f ? q4.x * qi : 1.0f;
+    const float qx = q4.y * qi, qy = q4.z * qi, qz = q4.w * qi;
+    float R[9];
+    R[0] = 1.0f - 2.0f * (qy * qy + qz * qz);
+    R[1] = 2.0f * (qx * qy - w * qz);
+    R[2] = 2.0f * (qx * qz + w * qy);
+    R[3] = 2.0f * (qx * qy + w * qz);
+    R[4] = 1.0f - 2.0f * (qx * qx + qz * qz);
+    R[5] = 2.0f * (qy * qz - w * qx);
+    R[6] = 2.0f * (qx * qz - w * qy);
+    R[7] = 2.0f * (qy * qz + w * qx);
+    R[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
+    const float opac = 1.0f / (1.0f + expf(-logit));
+
+    // adaptive filter (Eq. 6, 12, 13)
+    float kv = 0.0f;
+    if (!(fc.flags & AAAG_FLAG_NO_FILTER)) {
+      const float vhat = fc.fx / fmaxf(vz, fc.znear);
+      const float veff = fminf(vtrain, vhat);
+      kv = fc.k / (veff * veff);
+    }
+    const float s2x = sx * sx, s2y = sy * sy, s2z = sz * sz;
+    const float hx = s2x + kv, hy = s2y + kv, hz = s2z + kv;
+    // d = unit vector camera -> mean; d' = R^T d
+    const float dx0 = mx - fc.o[0], dy0 = my - fc.o[1], dz0 = mz - fc.o[2];
+    const float dist = sqrtf(dx0 * dx0 + dy0 * dy0 + dz0 * dz0);
+    const float idist = 1.0f / dist;
+    const float ddx = dx0 * idist, ddy = dy0 * idist, ddz = dz0 * idist;
+    const float p0 = R[0] * ddx + R[3] * ddy + R[6] * ddz;
+    const float p1 = R[1] * ddx + R[4] * ddy + R[7] * ddz;
+    const float p2 = R[2] * ddx + R[5] * ddy + R[8] * ddz;
+    // Eq. 12 divided through by s_hat_1 s_hat_2 s_hat_3: a weighted mean of
+    // r_j r_k with weights d'_i^2 / s_hat_i, r_j = s_j^2 / s_hat_j
+    const float w0 = p0 * p0 / hx, w1 = p1 * p1 / hy, w2 = p2 * p2 / hz;
+    const float r0 = s2x / hx, r1 = s2y / hy, r2 = s2z / hz;
+    const float phi2 = (w0 * r1 * r2 + w1 * r0 * r2 + w2 * r0 * r1) / (w0 + w1 + w2);
+    const float o_hat = opac * sqrtf(phi2);
+
+    if (o_hat > kAlphaMin) {
+      const float tau = 2.0f * logf(o_hat * 255.0f);
+      const float spx = sqrtf(hx), spy = sqrtf(hy), spz = sqrtf(hz);
+      // camera origin in normalised Gaussian space: S'^-1 R^T (o - mu)
+      const float ux = -dist * p0 / spx, uy = -dist * p1 / spy, uz = -dist * p2 / spz;
+      const bool inside = ux * ux + uy * uy + uz * uz < tau;
+      // A = Rv R S': rows are the view axes expressed in the Gaussian frame
+      float A[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float a0 = fc.Rv[3 * r + 0] * R[0] + fc.Rv[3 * r + 1] * R[3] + fc.Rv[3 * r + 2] * R[6];
+        const float a1 = fc.Rv[3 * r + 0] * R[1] + fc.Rv[3 * r + 1] * R[4] + fc.Rv[3 * r + 2] * R[7];
+        const float a2 = fc.Rv[3 * r + 0] * R[2] + fc.Rv[3 * r + 1] * R[5] + fc.Rv[3 * r + 2] * R[8];
+        A[3 * r + 0] = a0 * spx;
+        A[3 * r + 1] = a1 * spy;
+        A[3 * r + 2] = a2 * spz;
+      }
+      const float3 A1 = f3(A[0], A[1], A[2]), A2 = f3(A[3], A[4], A[5]), A3 = f3(A[6], A[7], A[8]);
+      const float tau_c = inflate_tau(tau);
+      const float zext = sqrtf(tau_c * dot3(A3, A3));
+      const float z_lo = vz - zext, z_hi = vz + zext;
+      int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+      bool ok = !inside && z_hi >= fc.znear;
+      if (ok) {
+        float px1, px2, py1, py2;
+        ok = axis_bounds(A1, A3, vx, vz, tau_c, fc.fx, fc.cx, fc.eps, px1, px2) &&
+             axis_bounds(A2, A3, vy, vz, tau_c, fc.fy, fc.cy, fc.eps, py1, py2) &&
+             tile_range(px1, px2, fc.W, fc.tiles_x, tx0, tx1) &&
+             tile_range(py1, py2, fc.H, fc.tiles_y, ty0, ty1);
+      }
+      const float4 t1 = make_float4(A[0], A[1], A[2], vx);
+      const float4 t2 = make_float4(A[3], A[4], A[5], vy);
+      const float4 t3 = make_float4(A[6], A[7], A[8], vz);
+      if (ok) {
+        // whole-image frustum cull (Sec. 3.4, last paragraph)
+        const float W = (float)fc.W, H = (float)fc.H;
+        ok = (z_lo < fc.znear)
+                 ? frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, 0.f, W, 0.f, H, tau_c)
+                 : frustum_hit<false>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, 0.f, W, 0.f, H, tau_c);
+      }
+      if (ok) {
+        visible = true;
+        // colour (view-dependent, real SH up to degree 3)
+        const int K = (s.sh_degree + 1) * (s.sh_degree + 1);
+        float Y[16];
+        sh_basis(ddx, ddy, ddz, s.sh_degree, Y);
+        float cr = 0.5f, cg = 0.5f, cb = 0.5f;
+        const float* shp = s.sh + (size_t)i * K * 3;
+        if (K == 16) {
+          const float4* s4 = reinterpret_cast<const float4*>(shp);
+          float c[48];
+#pragma unroll
+          for (int j = 0; j < 12; ++j) {
+            const float4 v = s4[j];
+            c[4 * j + 0] = v.x; c[4 * j + 1] = v.y; c[4 * j + 2] = v.z; c[4 * j + 3] = v.w;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            cr += Y[j] * c[3 * j + 0];
+            cg += Y[j] * c[3 * j + 1];
+            cb += Y[j] * c[3 * j + 2];
+          }
+        } else {
+          for (int j = 0; j < K; ++j) {
+            cr += Y[j] * shp[3 * j + 0];
+            cg += Y[j] * shp[3 * j + 1];
+            cb += Y[j] * shp[3 * j + 2];
+          }
+        }
+        Record out;
+        out.t1 = t1;
+        out.t2 = t2;
+        out.t3 = t3;
+        out.rgba = make_float4(fmaxf(cr, 0.0f), fmaxf(cg, 0.0f), fmaxf(cb, 0.0f), o_hat);
+        rec[i] = out;
+        // depth key: quantised max(z_lo, znear), rounded down
+        const float zk = fmaxf(z_lo, fc.znear);
+        uint32_t dk = (__float_as_uint(zk) - fc.znear_bits) >> fc.depth_shift;
+        const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
+        dk = min(dk, dmax);
+        aux[i] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16),
+                            __float_as_uint(tau), dk);
+        const uint32_t ntiles = (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1);
+        chunks[i] = (ntiles + 31u) / 32u;
+      }
+    }
+    if (!visible) {
+      aux[i] = make_uint4(1u, 0u, 0u, 0u);   // empty rectangle
+      chunks[i] = 0u;
+    }
+  }
+  const unsigned ball = __ballot_sync(0xffffffffu, visible);
+  if ((threadIdx.x & 31) == 0 && ball) atomicAdd(&stats[kStatVisible], (unsigned long long)__popc(ball));
+}
+
+}  // namespace
+
+aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_t st) {
+  if (s.n == 0) return AAAG_OK;
+  const int threads = 256;
+  const int64_t blocks = (s.n + threads - 1) / threads;
+  preprocess_kernel<<<(unsigned)blocks, threads, 0, st>>>(s, ws->fc, ws->records, ws->aux, ws->counts,
+                                                          ws->stats);
+  return check_launch("preprocess");
+}
+
+}  // namespace aaag

@@ -1,0 +1,290 @@
+// K3 + K4: stable LSD radix sort of the (key, Gaussian index) pairs and the
+// per-tile ranges (paper Sec. 3.1 'Blending Sort Order': tile-major, depth
+// minor).
+//
+// Onesweep structure: one histogram kernel reads every key once and counts
+// all digit positions; then one kernel per 8-bit digit ranks a 4096-key tile
+// per block (warp-level multisplit with __match_any_sync, preserving input
+// order), publishes its per-digit counts, resolves the exclusive prefix of
+// earlier tiles by decoupled look-back, and scatters through shared memory.
+// Tiles are taken in launch order from an atomic counter, so every tile a
+// block waits on belongs to a block that is already running.
+//
+// Look-back words are 64-bit: (epoch << 32) | (flag << 30) | count.  The epoch
+// (a device counter bumped by every sort, times 8 plus the pass) marks a word
+// as written by the current pass, so the look-back buffer never needs
+// clearing.  Every wait is bounded in time; on expiry the block sets a
+// timeout flag, proceeds with what it has and the frame is reported invalid.
+#include <algorithm>
+#include <utility>
+
+#include "aaag_internal.cuh"
+
+namespace aaag {
+namespace {
+
+constexpr int kRadix = 256;
+constexpr unsigned long long kFlagAggregate = 1ull << 30;
+constexpr unsigned long long kFlagPrefix = 2ull << 30;
+constexpr unsigned long long kCountMask = (1ull << 30) - 1ull;
+constexpr long long kWaitCycles = 2000000000ll;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__global__ void sort_init_kernel(uint32_t* hist, uint32_t* counters, unsigned long long* epoch) {
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) hist[i] = 0;
+  if (threadIdx.x < 4) counters[threadIdx.x] = 0;
+  if (threadIdx.x == 0) *epoch += 1ull;
+}
+
+__global__ void __launch_bounds__(256)
+sort_histogram_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev,
+                      int64_t n_max, int passes, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[4][kRadix];
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t n = min((int64_t)*n_dev, n_max);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = keys[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (8 * p)) & 0xffu], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    const uint32_t v = (&sh[0][0])[i];
+    if (v) atomicAdd(&hist[i], v);
+  }
+}
+
+// exclusive scan of 256 values held one per thread (blockDim == 256)
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t* tmp8) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) tmp8[warp] = x;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (int w = 0; w < warp; ++w) pre += tmp8[w];
+  __syncthreads();
+  return pre + x - v;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                 const uint32_t* __restrict__ n_dev, int64_t n_max, int pass,
+                 const uint32_t* __restrict__ hist, uint32_t* __restrict__ counter,
+                 unsigned long long* __restrict__ lookback,
+                 const unsigned long long* __restrict__ epoch_dev,
+                 unsigned long long* __restrict__ timeout_flag) {
+  __shared__ uint32_t s_keys[kSortTileKeys];
+  __shared__ uint32_t s_vals[kSortTileKeys];
+  __shared__ uint32_t s_warp[kSortThreads / 32][kRadix];   // per-warp digit counts -> prefixes
+  __shared__ uint32_t s_digit_start[kRadix];               // block-local digit starts
+  __shared__ uint32_t s_global[kRadix];                    // global start of this block's digits
+  __shared__ uint32_t s_tmp[8];
+  __shared__ int s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int shift = 8 * pass;
+  const int64_t n = min((int64_t)*n_dev, n_max);
+  const int64_t n_tiles = (n + kSortTileKeys - 1) / kSortTileKeys;
+  const unsigned long long epoch = ((*epoch_dev) * 8ull + (unsigned long long)pass) & 0xffffffffull;
+  const unsigned long long tag = epoch << 32;
+  // global exclusive offset of digit `tid` for this pass
+  const uint32_t gofs = block_exclusive_scan_256(hist[pass * kRadix + tid], s_tmp);
+
+  for (;;) {
+    if (tid == 0) s_tile = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= n_tiles) break;
+
+    // ---- load (warp-striped: coalesced) and rank within each warp
+    uint32_t k[kSortItems], v[kSortItems], r[kSortItems];
+    const int64_t base = tile * kSortTileKeys + (int64_t)warp * (32 * kSortItems);
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const int64_t idx = base + j * 32 + lane;
+      const bool ok = idx < n;
+      k[j] = ok ? keys_in[idx] : 0xffffffffu;
+      v[j] = ok ? vals_in[idx] : 0u;
+    }
+    for (int i = lane; i < kRadix; i += 32) s_warp[warp][i] = 0;
+    __syncwarp();
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const uint32_t d = (k[j] >> shift) & 0xffu;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t before = s_warp[warp][d];
+      __syncwarp();
+      if ((peers & lt) == 0) s_warp[warp][d] = before + __popc(peers);
+      __syncwarp();
+      r[j] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+
+    // ---- per digit (thread tid = digit): warp prefixes and block count
+    uint32_t count = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+      const uint32_t c = s_warp[w][tid];
+      s_warp[w][tid] = count;
+      count += c;
+    }
+    volatile unsigned long long* lb = lookback;
+    if (tile == 0) {
+      lb[tid] = tag | kFlagPrefix | count;
+    } else {
+      lb[tile * kRadix + tid] = tag | kFlagAggregate | count;
+    }
+    const uint32_t local_start = block_exclusive_scan_256(count, s_tmp);
+    s_digit_start[tid] = local_start;
+
+    // ---- decoupled look-back for digit tid
+    uint32_t prefix = 0;
+    if (tile > 0) {
+      int64_t t = tile - 1;
+      const long long t0 = clock64();
+      bool timed_out = false;
+      while (t >= 0) {
+        unsigned long long w = lb[t * kRadix + tid];
+        while ((w & 0xffffffff00000000ull) != tag || (w & (3ull << 30)) == 0) {
+          if (clock64() - t0 > kWaitCycles) {
+            timed_out = true;
+            break;
+          }
+          __nanosleep(20);
+          w = lb[t * kRadix + tid];
+        }
+        if (timed_out) break;
+        prefix += (uint32_t)(w & kCountMask);
+        if (w & kFlagPrefix) break;
+        --t;
+      }
+      if (timed_out) atomicExch(timeout_flag, 1ull);
+      lb[tile * kRadix + tid] = tag | kFlagPrefix | (unsigned long long)(prefix + count);
+    }
+    s_global[tid] = gofs + prefix;
+    __syncthreads();
+
+    // ---- scatter into shared memory in digit order, then to global memory
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const uint32_t d = (k[j] >> shift) & 0xffu;
+      const uint32_t pos = s_digit_start[d] + s_warp[warp][d] + r[j];
+      s_keys[pos] = k[j];
+      s_vals[pos] = v[j];
+    }
+    __syncthreads();
+    const int64_t valid = min((int64_t)kSortTileKeys, n - tile * kSortTileKeys);
+    for (int q = tid; q < kSortTileKeys; q += kSortThreads) {
+      const uint32_t key = s_keys[q];
+      const uint32_t d = (key >> shift) & 0xffu;
+      const int64_t g = (int64_t)s_global[d] + (q - (int64_t)s_digit_start[d]);
+      if (q < valid || g < n) {
+        if (g < n) {
+          keys_out[g] = key;
+          vals_out[g] = s_vals[q];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev,
+                              int64_t n_max, int depth_bits, uint2* __restrict__ ranges) {
+  const int64_t n = min((int64_t)*n_dev, n_max);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t t = keys[i] >> depth_bits;
+    if (i == 0 || (keys[i - 1] >> depth_bits) != t) ranges[t].x = (uint32_t)i;
+    if (i == n - 1 || (keys[i + 1] >> depth_bits) != t) ranges[t].y = (uint32_t)(i + 1);
+  }
+}
+
+int g_sm_count = 0;
+int g_pass_blocks_per_sm = 0;
+
+void init_occupancy() {
+  if (g_sm_count) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pass_blocks_per_sm, sort_pass_kernel, kSortThreads, 0);
+  if (g_pass_blocks_per_sm < 1) g_pass_blocks_per_sm = 1;
+  if (g_sm_count < 1) g_sm_count = 1;
+}
+
+}  // namespace
+
+size_t radix_sort_scratch(int64_t n_max) {
+  const int64_t tiles = (n_max + kSortTileKeys - 1) / kSortTileKeys;
+  // hist [4][256] u32, counters [4] u32 (padded), lookback [tiles][256] u64, epoch u64, n u32
+  return 4 * kRadix * 4 + 256 + (size_t)(tiles > 0 ? tiles : 1) * kRadix * 8 + 256;
+}
+
+aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                                uint32_t* vals_alt, const uint32_t* n_dev, int64_t n_max,
+                                int key_bits, uint32_t* hist, uint32_t* counters,
+                                unsigned long long* lookback, unsigned long long* epoch,
+                                unsigned long long* timeout_flag, int* result_in_alt,
+                                cudaStream_t st) {
+  const int passes = (key_bits + 7) / 8;
+  *result_in_alt = passes & 1;
+  if (n_max <= 0 || passes == 0) {
+    *result_in_alt = 0;
+    return AAAG_OK;
+  }
+  init_occupancy();
+  sort_init_kernel<<<1, 256, 0, st>>>(hist, counters, epoch);
+  const int64_t hblocks = std::min<int64_t>((n_max + 4095) / 4096, (int64_t)g_sm_count * 4);
+  sort_histogram_kernel<<<(unsigned)hblocks, 256, 0, st>>>(keys, n_dev, n_max, passes, hist);
+  aaag_status e = check_launch("sort_histogram");
+  if (e != AAAG_OK) return e;
+  const int64_t tiles = (n_max + kSortTileKeys - 1) / kSortTileKeys;
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)g_sm_count * g_pass_blocks_per_sm);
+  uint32_t* kin = keys;
+  uint32_t* vin = vals;
+  uint32_t* kout = keys_alt;
+  uint32_t* vout = vals_alt;
+  for (int p = 0; p < passes; ++p) {
+    sort_pass_kernel<<<(unsigned)grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_dev, n_max, p, hist,
+                                                               counters + p, lookback, epoch, timeout_flag);
+    e = check_launch("sort_pass");
+    if (e != AAAG_OK) return e;
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  return AAAG_OK;
+}
+
+aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st) {
+  // device-side pair count, clipped to the capacity by the pair scan of K2
+  const uint32_t* n_dev = reinterpret_cast<const uint32_t*>(ws->stats + kStatPairsClipped);
+  int alt = 0;
+  aaag_status e = radix_sort_device_n(ws->keys[0], ws->vals[0], ws->keys[1], ws->vals[1], n_dev, ws->capacity, 32,
+                          ws->sort_hist, ws->sort_counters, ws->sort_lookback,
+                          ws->stats + kStatSortEpoch, ws->stats + kStatTimeout, &alt, st);
+  if (e != AAAG_OK) return e;
+  ws->sorted_in_alt = alt;
+  if (cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * (size_t)ws->n_tiles, st) != cudaSuccess)
+    return check_launch("ranges memset");
+  init_occupancy();
+  const int64_t rblocks = std::min<int64_t>((ws->capacity + 255) / 256, (int64_t)g_sm_count * 8);
+  ranges_kernel<<<(unsigned)std::max<int64_t>(rblocks, 1), 256, 0, st>>>(
+      ws->keys[alt], n_dev, ws->capacity, ws->fc.depth_bits, ws->ranges);
+  return check_launch("ranges");
+}
+
+}  // namespace aaag

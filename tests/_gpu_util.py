@@ -1,0 +1,87 @@
+"""Helpers shared by the GPU tests: run the CUDA path through the C-ABI binding
+and compare with the oracle."""
+import math
+
+import numpy as np
+import torch
+
+import oracle as O
+from paper_2504_12811_gb300 import aaag, scenes
+
+TOL_ABS = 2e-3        # max abs error on non-ambiguous pixels
+TOL_PSNR = 55.0       # dB over all pixels
+TOL_AMBIG = 2e-3      # largest allowed fraction of ambiguous pixels
+
+
+def run_frame(scene, cam, capacity=None, params=None, stages=("pre", "cull", "sort", "render")):
+    """Run the requested stages on a fresh workspace; returns (ws, rgb, alpha, dscene)."""
+    ds = aaag.DeviceScene(scene)
+    cap = capacity if capacity is not None else max(1 << 16, 64 * scene.n)
+    ws = aaag.Workspace(scene.n, cam.width, cam.height, cap)
+    st = aaag.current_stream()
+    prm = params if params is not None else aaag.make_params()
+    rgb = torch.full((3, cam.height, cam.width), float("nan"), device="cuda")
+    alpha = torch.full((cam.height, cam.width), float("nan"), device="cuda")
+    if "pre" in stages:
+        aaag.aaag_preprocess(ds.struct(), aaag.make_camera(cam), prm, ws.handle, st)
+    if "cull" in stages:
+        aaag.aaag_cull(ws.handle, st)
+    if "sort" in stages:
+        aaag.aaag_sort(ws.handle, st)
+    if "render" in stages:
+        aaag.aaag_render(ws.handle, rgb.data_ptr(), alpha.data_ptr(), st)
+    torch.cuda.synchronize()
+    return ws, rgb, alpha, ds
+
+
+def dev_array(ws, ptr, count, dtype):
+    """Copy `count` elements of a workspace array (device pointer into the
+    workspace buffer) to numpy, by slicing the torch tensor that backs it."""
+    itemsize = np.dtype(dtype).itemsize
+    if count == 0:
+        return np.empty(0, dtype=dtype)
+    off = int(ptr) - ws.buffer.data_ptr()
+    assert 0 <= off and off + count * itemsize <= ws.buffer.numel()
+    torch.cuda.synchronize()
+    raw = ws.buffer[off:off + count * itemsize].cpu().numpy()
+    return raw.view(dtype).copy()
+
+
+def stats(ws):
+    return aaag.stats(ws, check=False)
+
+
+def psnr(a, b):
+    mse = float(np.mean((a - b) ** 2))
+    return math.inf if mse == 0 else 10 * math.log10(1.0 / mse)
+
+
+def compare_image(gpu_rgb, gpu_alpha, ref_rgb, ref_alpha, ambiguous):
+    """Returns a dict of error figures; `ambiguous` [H,W] bool."""
+    g = gpu_rgb.detach().cpu().numpy().astype(np.float64)
+    ga = gpu_alpha.detach().cpu().numpy().astype(np.float64)
+    r = ref_rgb.numpy() if torch.is_tensor(ref_rgb) else ref_rgb
+    ra = ref_alpha.numpy() if torch.is_tensor(ref_alpha) else ref_alpha
+    err = np.abs(g - r).max(0)
+    err = np.maximum(err, np.abs(ga - ra))
+    clean = ~ambiguous
+    return {
+        "max_abs_clean": float(err[clean].max()) if clean.any() else 0.0,
+        "max_abs_all": float(err.max()),
+        "psnr_rgb": psnr(g, r),
+        "psnr_alpha": psnr(ga, ra),
+        "ambiguous_fraction": float(ambiguous.mean()),
+        "finite": bool(np.isfinite(g).all() and np.isfinite(ga).all()),
+    }
+
+
+def oracle_image_and_mask(scene, cam):
+    prep = O.prepare(scene, cam)
+    rgb, alpha = O.render(scene, cam, prep=prep)
+    py, px = np.mgrid[0:cam.height, 0:cam.width]
+    mask = []
+    step = 2048
+    fx, fy = px.ravel(), py.ravel()
+    for i in range(0, fx.size, step):
+        mask.append(O.ambiguous_pixels(prep, fx[i:i + step], fy[i:i + step]).numpy())
+    return prep, rgb, alpha, np.concatenate(mask).reshape(cam.height, cam.width)

@@ -1,0 +1,49 @@
+"""Parity at the full benchmark size: 1M Gaussians, 1920x1080, in the launch
+configuration bench.py times (same workspace capacity), on pixels sampled at
+random and computed one by one by the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2504_12811_gb300 import aaag, scenes
+from _gpu_util import TOL_ABS, TOL_AMBIG, TOL_PSNR, psnr
+
+pytestmark = pytest.mark.gpu
+
+BENCH_CAPACITY = 48 << 20
+
+
+@pytest.fixture(scope="module")
+def scene1m():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_12811_gb300 import build
+    build.build()
+    return scenes.workload("scene1m")
+
+
+@pytest.mark.parametrize("pose", [0, 5])
+def test_scene1m_sampled_pixels(scene1m, pose):
+    scene, poses = scene1m
+    cam = poses[pose]
+    ds = aaag.DeviceScene(scene)
+    ws = aaag.Workspace(scene.n, cam.width, cam.height, BENCH_CAPACITY)
+    rgb, alpha = aaag.render(ds, cam, ws)
+    st = aaag.stats(ws)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11 + pose)
+    m = 480
+    px = rng.integers(0, cam.width, m)
+    py = rng.integers(0, cam.height, m)
+    prep = O.prepare(scene, cam)
+    ref, ref_a = O.render_pixels(scene, cam, px, py, prep=prep)
+    amb = O.ambiguous_pixels(prep, px, py).numpy()
+    g = rgb.cpu().numpy()[:, py, px].T.astype(np.float64)
+    ga = alpha.cpu().numpy()[py, px].astype(np.float64)
+    err = np.maximum(np.abs(g - ref.numpy()).max(1), np.abs(ga - ref_a.numpy()))
+    print(f"pose {pose}: stats={st} max|err| clean={err[~amb].max():.3e} all={err.max():.3e} "
+          f"ambiguous={amb.mean():.4f} psnr={psnr(g, ref.numpy()):.1f}")
+    assert amb.mean() < TOL_AMBIG * 5
+    assert err[~amb].max() <= TOL_ABS
+    assert psnr(g, ref.numpy()) >= TOL_PSNR
