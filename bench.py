@@ -29,7 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "1080p frames/s @1M Gaussians (fwd)"
+METRIC = "1080p frames/s @1M Gaussians (fwd)"  # fwd+bwd reported under "fwd_bwd"
 WORKLOAD = "scene1m: 1,000,000 Gaussians (64 clusters + 10% shell, SH 3), 1920x1080, 16 poses"
 
 # algorithmic FP32 operations per pixel x Gaussian evaluation in the render
@@ -266,6 +266,30 @@ def run_ours(args):
     frames = args.steps * world
     value = frames / (total_ms / 1e3)
 
+    # ---- forward + backward (gradients w.r.t. every scene parameter)
+    grads = [torch.empty_like(t) for t in (ds.means, ds.log_scales, ds.quats, ds.opacity_logits, ds.sh)]
+    gstruct = aaag.aaag_grads(*[t.data_ptr() for t in grads])
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    drgb = torch.randn(3, H, W, device=dev, generator=g)
+    dalpha = torch.randn(H, W, device=dev, generator=g)
+    bwd_steps = max(4, args.steps // 2)
+    bev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(bwd_steps)]
+    torch.cuda.synchronize()
+    for k in range(bwd_steps):
+        flush.zero_()
+        bev[k][0].record(stream)
+        frame(args.warmup + k)
+        bev[k][1].record(stream)
+        aaag.aaag_render_backward(scene_struct, ws.handle, rgb.data_ptr(), drgb.data_ptr(), dalpha.data_ptr(),
+                                  gstruct, sptr)
+        bev[k][2].record(stream)
+    torch.cuda.synchronize()
+    st_b = aaag.stats(ws, check=False)
+    fb_ms = np.array([[bev[k][0].elapsed_time(bev[k][1]), bev[k][1].elapsed_time(bev[k][2])]
+                      for k in range(bwd_steps)])
+    fwd_bwd_fps = bwd_steps / (fb_ms.sum() / 1e3) * world
+
     # ---- roofline of the dominant kernel (render, FP32 ALU bound)
     ev_by_step = [per_pose[(args.warmup + k) % len(poses)]["evaluations"] for k in range(args.steps)]
     render_ms = stage[:, 3]
@@ -324,6 +348,9 @@ def run_ours(args):
                       "evaluations": mean("evaluations"), "blended": mean("blended"),
                       "misorders": mean("misorders"), "tiles_tested": mean("tiles_tested")},
         "evals_per_s": float(np.sum(ev_by_step) / (total_ms / 1e3)),
+        "fwd_bwd": {"value": fwd_bwd_fps, "unit": "frames/s", "forward_ms": float(fb_ms[:, 0].mean()),
+                    "backward_ms": float(fb_ms[:, 1].mean()), "steps": bwd_steps,
+                    "replay_mismatch": int(st_b["replay_mismatch"])},
         "roofline": {"kernel": "render", "bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops, "traffic": None,
                      "peak_source": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",

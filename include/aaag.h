@@ -100,6 +100,8 @@ typedef struct {
   uint64_t evaluations;    /* pixel x Gaussian evaluations in aaag_render   */
   uint64_t blended;        /* contributors blended                          */
   uint64_t misorders;      /* forced emissions of the per-pixel buffer      */
+  uint64_t replay_mismatch;/* pixels whose backward replay blended a count
+                              different from the forward pass (expected 0)  */
   uint32_t capacity_overflow;  /* 1 when n_pairs > pair_capacity            */
   uint32_t timeout;            /* 1 when a bounded device wait gave up       */
 } aaag_stats;
@@ -214,6 +216,26 @@ aaag_status aaag_sort(aaag_workspace* ws, cudaStream_t stream);
  * ------------------------------------------------------------------------ */
 aaag_status aaag_render(aaag_workspace* ws, float* rgb, float* alpha,
                         cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
+ * aaag_render_backward -- gradients of a scalar loss L with respect to the
+ * scene parameters, given dL/drgb [3][H][W] and optionally dL/dalpha [H][W]
+ * (NULL = 0) for the frame last rendered with this workspace (the workspace
+ * must be untouched since aaag_render).  `rgb` is that frame's output.  The
+ * pass replays each pixel's blend sequence and differentiates front-to-back
+ * compositing using the stored final transmittance (S_i = rgb - C_{<=i}), the
+ * maximum response of Sec. 3.1 through the planes of Eq. 4-5, the filtered
+ * opacity of Eq. 12-13, the activations, and the SH colour.  Discrete
+ * decisions (discards, bounds, culling, the alpha and colour clamps, early
+ * termination) are held fixed.  Writes every entry of *grads (device arrays,
+ * caller-owned, layout of aaag_scene; zero for Gaussians not visible).
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ * ------------------------------------------------------------------------ */
+aaag_status aaag_render_backward(const aaag_scene* scene /* host struct */,
+                                 aaag_workspace* ws, const float* rgb,
+                                 const float* dL_drgb, const float* dL_dalpha,
+                                 const aaag_grads* grads /* host struct */,
+                                 cudaStream_t stream);
 
 /* Convenience: preprocess + cull + sort + render in one call. */
 aaag_status aaag_render_frame(const aaag_scene* scene, const aaag_camera* camera,

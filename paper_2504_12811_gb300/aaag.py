@@ -46,7 +46,7 @@ class aaag_stats(C.Structure):
     _fields_ = [("n_gaussians", C.c_uint64), ("n_visible", C.c_uint64), ("n_pairs", C.c_uint64),
                 ("pair_capacity", C.c_uint64), ("tiles_tested", C.c_uint64),
                 ("evaluations", C.c_uint64), ("blended", C.c_uint64), ("misorders", C.c_uint64),
-                ("capacity_overflow", C.c_uint32), ("timeout", C.c_uint32)]
+                ("replay_mismatch", C.c_uint64), ("capacity_overflow", C.c_uint32), ("timeout", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -79,6 +79,8 @@ SIGNATURES = [
     ("aaag_render", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("aaag_render_frame", C.c_int, [C.POINTER(aaag_scene), C.POINTER(aaag_camera), C.POINTER(aaag_params),
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("aaag_render_backward", C.c_int, [C.POINTER(aaag_scene), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.POINTER(aaag_grads), C.c_void_p]),
     ("aaag_radix_sort_scratch_bytes", C.c_size_t, [C.c_int64]),
     ("aaag_radix_sort", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                   C.c_void_p, C.c_size_t, C.POINTER(C.c_int32), C.c_void_p]),
@@ -157,6 +159,11 @@ def aaag_render_frame(scene, camera, params, ws, rgb_ptr, alpha_ptr, stream):
     _check(lib().aaag_render_frame(C.byref(scene), C.byref(camera),
                                    C.byref(params) if params is not None else None, ws,
                                    rgb_ptr, alpha_ptr, stream), "aaag_render_frame")
+
+
+def aaag_render_backward(scene, ws, rgb_ptr, drgb_ptr, dalpha_ptr, grads, stream):
+    _check(lib().aaag_render_backward(C.byref(scene), ws, rgb_ptr, drgb_ptr, dalpha_ptr, C.byref(grads), stream),
+           "aaag_render_backward")
 
 
 def aaag_radix_sort_scratch_bytes(n):

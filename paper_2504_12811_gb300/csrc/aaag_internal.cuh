@@ -68,6 +68,7 @@ enum StatSlot : int {
   kStatTimeout = 7,
   kStatSortEpoch = 8,
   kStatChunks = 9,         // chunks of 32 candidate tiles (K2 work items)
+  kStatReplayMismatch = 10,// pixels whose backward replay blended a different count
   kStatChunksClipped = 14, // uint32: chunk count clipped to the chunk capacity
   kStatPairsClipped = 15,  // uint32: pair count clipped to the pair capacity
   kStatCount = 16
@@ -100,6 +101,7 @@ struct aaag_workspace {
   float* final_T;                // [H*W]
   uint32_t* n_blended;           // [H*W]
   unsigned long long* stats;     // [kStatCount]
+  float4* grad_acc;              // [n][4] backward accumulators (dt1, dt2, dt3, colour + o_hat)
   aaag::FrameConst fc;
   bool have_frame;
   int sorted_in_alt;             // which buffer holds the sorted pairs
@@ -120,6 +122,8 @@ aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_
 aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st);
+aaag_status launch_render_backward(const SceneDev& s, aaag_workspace* ws, const float* rgb, const float* drgb,
+                                   const float* dalpha, const aaag_grads* out, cudaStream_t st);
 aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                                 uint32_t* vals_alt, const uint32_t* n_dev, int64_t n_max,
                                 int key_bits, uint32_t* hist, uint32_t* counters,

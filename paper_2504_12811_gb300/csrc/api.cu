@@ -36,7 +36,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
   size_t records, aux, counts, offsets, partials, owner, mask, pofs, keys0, keys1, vals0, vals1, hist, counters,
-      lookback, ranges, final_T, n_blended, stats, total;
+      lookback, ranges, final_T, n_blended, stats, grad, total;
 };
 
 int tiles_of(int size) { return (size + kTile - 1) / kTile; }
@@ -76,6 +76,7 @@ Layout layout_of(int64_t n, int w, int h, int64_t cap) {
   L.final_T = take((size_t)w * h * 4);
   L.n_blended = take((size_t)w * h * 4);
   L.stats = take(kStatCount * 8);
+  L.grad = take((size_t)n * 64);
   L.total = off;
   return L;
 }
@@ -148,6 +149,40 @@ aaag_status make_frame(const aaag_camera* cam, const aaag_params* prm, int sh_de
 
 __global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
 
+SceneDev scene_dev(const aaag_scene* scene) {
+  SceneDev s;
+  s.n = scene->n;
+  s.sh_degree = scene->sh_degree;
+  s.means = scene->means;
+  s.log_scales = scene->log_scales;
+  s.quats = scene->quats;
+  s.opacity_logits = scene->opacity_logits;
+  s.sh = scene->sh;
+  s.vhat_train = scene->vhat_train;
+  return s;
+}
+
+aaag_status check_scene(const aaag_scene* scene, const aaag_workspace* ws, const char* who) {
+  if (scene->n != ws->n) {
+    set_error("%s: scene has %lld Gaussians, the workspace %lld", who, (long long)scene->n, (long long)ws->n);
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (scene->sh_degree < 0 || scene->sh_degree > kMaxShDegree) {
+    set_error("%s: sh_degree %d not in 0..3", who, scene->sh_degree);
+    return AAAG_ERR_UNSUPPORTED;
+  }
+  if (scene->n > 0 && (!scene->means || !scene->log_scales || !scene->quats || !scene->opacity_logits ||
+                       !scene->sh || !scene->vhat_train)) {
+    set_error("%s: null scene array", who);
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (((uintptr_t)scene->quats) % 16 || ((uintptr_t)scene->sh) % 16) {
+    set_error("%s: quats and sh must be 16-byte aligned", who);
+    return AAAG_ERR_INVALID_ARG;
+  }
+  return AAAG_OK;
+}
+
 }  // namespace
 }  // namespace aaag
 
@@ -217,6 +252,7 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
   w->final_T = reinterpret_cast<float*>(b + L.final_T);
   w->n_blended = reinterpret_cast<uint32_t*>(b + L.n_blended);
   w->stats = reinterpret_cast<unsigned long long*>(b + L.stats);
+  w->grad_acc = reinterpret_cast<float4*>(b + L.grad);
   w->n_scan_blocks = (n + 4095) / 4096;
   w->n_sort_tiles = (pair_capacity + kSortTileKeys - 1) / kSortTileKeys;
   // the look-back epoch lives in the stats block and must start defined; the
@@ -267,18 +303,9 @@ aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, 
               (long long)scene->n, camera->width, camera->height, (long long)ws->n, ws->width, ws->height);
     return AAAG_ERR_INVALID_ARG;
   }
-  if (scene->sh_degree < 0 || scene->sh_degree > kMaxShDegree) {
-    set_error("aaag_preprocess: sh_degree %d not in 0..3", scene->sh_degree);
-    return AAAG_ERR_UNSUPPORTED;
-  }
-  if (scene->n > 0 && (!scene->means || !scene->log_scales || !scene->quats || !scene->opacity_logits ||
-                       !scene->sh || !scene->vhat_train)) {
-    set_error("aaag_preprocess: null scene array");
-    return AAAG_ERR_INVALID_ARG;
-  }
-  if (((uintptr_t)scene->quats) % 16 || ((uintptr_t)scene->sh) % 16) {
-    set_error("aaag_preprocess: quats and sh must be 16-byte aligned");
-    return AAAG_ERR_INVALID_ARG;
+  {
+    const aaag_status e = check_scene(scene, ws, "aaag_preprocess");
+    if (e != AAAG_OK) return e;
   }
   if (!finite_camera(camera)) {
     set_error("aaag_preprocess: camera has non-finite or non-positive fields");
@@ -298,16 +325,7 @@ aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, 
   // reset per-frame statistics (keep the sort epoch)
   if (cudaMemsetAsync(ws->stats, 0, kStatSortEpoch * 8, stream) != cudaSuccess)
     return check_launch("preprocess memset");
-  SceneDev s;
-  s.n = scene->n;
-  s.sh_degree = scene->sh_degree;
-  s.means = scene->means;
-  s.log_scales = scene->log_scales;
-  s.quats = scene->quats;
-  s.opacity_logits = scene->opacity_logits;
-  s.sh = scene->sh;
-  s.vhat_train = scene->vhat_train;
-  return launch_preprocess(s, ws, stream);
+  return launch_preprocess(scene_dev(scene), ws, stream);
 }
 
 aaag_status aaag_cull(aaag_workspace* ws, cudaStream_t stream) {
@@ -341,6 +359,29 @@ aaag_status aaag_render_frame(const aaag_scene* scene, const aaag_camera* camera
   if (e == AAAG_OK) e = aaag_sort(ws, stream);
   if (e == AAAG_OK) e = aaag_render(ws, rgb, alpha, stream);
   return e;
+}
+
+aaag_status aaag_render_backward(const aaag_scene* scene, aaag_workspace* ws, const float* rgb,
+                                 const float* dL_drgb, const float* dL_dalpha, const aaag_grads* grads,
+                                 cudaStream_t stream) {
+  if (!scene || !ws || !ws->have_frame || !rgb || !dL_drgb || !grads) {
+    set_error("aaag_render_backward: null argument or no rendered frame");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  aaag_status e = check_scene(scene, ws, "aaag_render_backward");
+  if (e != AAAG_OK) return e;
+  if (scene->sh_degree != ws->fc.sh_degree) {
+    set_error("aaag_render_backward: scene differs from the preprocessed one");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (scene->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits ||
+                       !grads->sh)) {
+    set_error("aaag_render_backward: null gradient array");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (cudaMemsetAsync(ws->stats + kStatReplayMismatch, 0, 8, stream) != cudaSuccess)
+    return check_launch("backward memset");
+  return launch_render_backward(scene_dev(scene), ws, rgb, dL_drgb, dL_dalpha, grads, stream);
 }
 
 size_t aaag_radix_sort_scratch_bytes(int64_t n) { return n < 0 ? 0 : radix_sort_scratch(n); }
@@ -401,6 +442,7 @@ aaag_status aaag_get_stats(aaag_workspace* ws, aaag_stats* out, cudaStream_t str
   out->misorders = h[kStatMisorders];
   out->capacity_overflow = (uint32_t)h[kStatOverflow];
   out->timeout = (uint32_t)h[kStatTimeout];
+  out->replay_mismatch = h[kStatReplayMismatch];
   if (out->capacity_overflow) {
     set_error("pair capacity %lld exceeded: %llu pairs", (long long)ws->capacity, (unsigned long long)h[kStatPairs]);
     return AAAG_ERR_CAPACITY;

@@ -1,0 +1,388 @@
+// K6 + K7: gradients of the rendered image with respect to the scene
+// parameters (means, log-scales, quaternions, opacity logits, SH).
+//
+// K6 (render backward) replays the forward traversal of every tile with the
+// same code (render_core.cuh), so it blends the same contributors in the same
+// order.  Compositing is differentiated front to back: with the forward output
+// F = C_final + T_final bg known, the colour behind contributor i after it is
+// blended is S_i = F - C_{<=i}, so
+//   dF/dc_i     = alpha_i T_i
+//   dF/dalpha_i = c_i T_i - S_i / (1 - alpha_i)
+//   dA/dalpha_i = T_final / (1 - alpha_i)            (A = 1 - T_final)
+// No per-blend state is cached.  For each blended contributor the pixel's two
+// transformed planes are recomputed (Eq. 4-5), rho^2 = |num|^2/|d|^2 is
+// differentiated back to the rows t1, t2, t3 of T_view, and the 16 values
+// (dt1, dt2, dt3, dcolour, do_hat) are added to a per-Gaussian accumulator
+// with vector atomics.
+//
+// K7 (preprocess backward) is one thread per Gaussian: it recomputes the
+// forward preprocessing and applies the chain rule through T_view = Rv R S'
+// and mu_v, the filtered scales s' = sqrt(s^2 + k / v'^2), the amplitude
+// factor of Eq. 12 (and v' = min(v_train, f / z) when the view term is the
+// active branch), the opacity sigmoid, the quaternion normalisation and the SH
+// colour with its viewing direction.  Discrete decisions (discards, bounds,
+// culling, clamps) are held fixed.
+#include <algorithm>
+
+#include "aaag_internal.cuh"
+#include "render_core.cuh"
+
+namespace aaag {
+namespace {
+
+struct BackwardBlend {
+  const Record* rec;
+  float4* grad;        // [n][4] accumulators: dt1, dt2, dt3, (dr, dg, db, do_hat)
+  const FrameConst* fc;
+  float T, Cr, Cg, Cb;
+  bool done;
+  uint32_t nblend;
+  float X, Y;          // absolute pixel centre
+  float gr, gg, gb;    // dL/dRGB
+  float ga;            // dL/dalpha (output alpha)
+  float Fr, Fg, Fb;    // forward output colour (includes T_final bg)
+  float Tfinal;
+
+  __device__ __forceinline__ void blend(float a, uint32_t gid) {
+    const float Tn = T * (1.0f - a);
+    if (Tn < kTStop) {
+      done = true;
+      return;
+    }
+    const float4* r = reinterpret_cast<const float4*>(rec + gid);
+    const float4 c = __ldg(r + 3);
+    const float w = a * T;
+    Cr = fmaf(c.x, w, Cr);
+    Cg = fmaf(c.y, w, Cg);
+    Cb = fmaf(c.z, w, Cb);
+    const float inv1ma = 1.0f / (1.0f - a);
+    // dL/dalpha from the colour and the output alpha
+    const float dal = gr * (c.x * T - (Fr - Cr) * inv1ma) + gg * (c.y * T - (Fg - Cg) * inv1ma) +
+                      gb * (c.z * T - (Fb - Cb) * inv1ma) + ga * Tfinal * inv1ma;
+    // alpha = min(0.99, o_hat exp(-rho^2/2)): recompute rho^2 at this pixel
+    const float4 t1 = __ldg(r + 0), t2 = __ldg(r + 1), t3 = __ldg(r + 2);
+    const float cxm = fc->cx - X, cym = fc->cy - Y;
+    const float3 n1 = f3(fmaf(cxm, t3.x, fc->fx * t1.x), fmaf(cxm, t3.y, fc->fx * t1.y), fmaf(cxm, t3.z, fc->fx * t1.z));
+    const float h1 = fmaf(cxm, t3.w, fc->fx * t1.w);
+    const float3 n2 = f3(fmaf(cym, t3.x, fc->fy * t2.x), fmaf(cym, t3.y, fc->fy * t2.y), fmaf(cym, t3.z, fc->fy * t2.z));
+    const float h2 = fmaf(cym, t3.w, fc->fy * t2.w);
+    const float3 num = h1 * n2 - h2 * n1;
+    const float3 dv = cross3(n1, n2);
+    const float inv = 1.0f / dot3(dv, dv);
+    const float rho2 = dot3(num, num) * inv;
+    const float G = __expf(-0.5f * rho2);
+    const float raw = c.w * G;
+    float4 g1 = make_float4(0.f, 0.f, 0.f, 0.f), g2 = g1, g3 = g1;
+    float doh = 0.0f;
+    if (raw < kAlphaMax) {
+      doh = dal * G;
+      const float drho2 = -0.5f * dal * raw;
+      const float3 dnum = (2.0f * drho2 * inv) * num;
+      const float3 ddv = (-2.0f * drho2 * rho2 * inv) * dv;
+      const float dh1 = dot3(n2, dnum), dh2 = -dot3(n1, dnum);
+      const float3 dn1 = (-h2) * dnum + cross3(n2, ddv);
+      const float3 dn2 = h1 * dnum + cross3(ddv, n1);
+      g1 = make_float4(fc->fx * dn1.x, fc->fx * dn1.y, fc->fx * dn1.z, fc->fx * dh1);
+      g2 = make_float4(fc->fy * dn2.x, fc->fy * dn2.y, fc->fy * dn2.z, fc->fy * dh2);
+      g3 = make_float4(cxm * dn1.x + cym * dn2.x, cxm * dn1.y + cym * dn2.y, cxm * dn1.z + cym * dn2.z,
+                       cxm * dh1 + cym * dh2);
+    }
+    float4* acc = grad + 4 * (size_t)gid;
+    atomicAdd(acc + 0, g1);
+    atomicAdd(acc + 1, g2);
+    atomicAdd(acc + 2, g3);
+    atomicAdd(acc + 3, make_float4(gr * w, gg * w, gb * w, doh));
+    T = Tn;
+    ++nblend;
+  }
+};
+
+__global__ void __launch_bounds__(kTilePixels, 2)
+render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
+                       const uint32_t* __restrict__ vals, const Record* __restrict__ rec, FrameConst fc,
+                       const float* __restrict__ rgb, const float* __restrict__ drgb,
+                       const float* __restrict__ dalpha, const float* __restrict__ final_T,
+                       const uint32_t* __restrict__ n_blended, float4* __restrict__ grad,
+                       unsigned long long* __restrict__ stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileSmem& s = *reinterpret_cast<TileSmem*>(smem_raw);
+  const int tile = blockIdx.x;
+  const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
+  const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+  const int px = tx * kTile + lx, py = ty * kTile + ly;
+  const bool in_image = px < fc.W && py < fc.H;
+  const size_t HW = (size_t)fc.W * fc.H;
+  const size_t p = in_image ? (size_t)py * fc.W + px : 0;
+
+  BackwardBlend bl;
+  bl.rec = rec;
+  bl.grad = grad;
+  bl.fc = &fc;
+  bl.T = 1.0f;
+  bl.Cr = bl.Cg = bl.Cb = 0.0f;
+  bl.nblend = 0;
+  bl.X = (float)px + 0.5f;
+  bl.Y = (float)py + 0.5f;
+  float Tf = 1.0f;
+  if (in_image) {
+    bl.gr = drgb[p];
+    bl.gg = drgb[HW + p];
+    bl.gb = drgb[2 * HW + p];
+    bl.ga = dalpha ? dalpha[p] : 0.0f;
+    bl.Fr = rgb[p];
+    bl.Fg = rgb[HW + p];
+    bl.Fb = rgb[2 * HW + p];
+    Tf = final_T[p];
+  } else {
+    bl.gr = bl.gg = bl.gb = bl.ga = bl.Fr = bl.Fg = bl.Fb = 0.0f;
+  }
+  bl.Tfinal = Tf;
+  // a pixel with no incoming gradient still replays (the block walks in
+  // lockstep) but skips its blends
+  bl.done = !in_image;
+  unsigned long long neval = 0;
+  uint32_t nmis = 0;
+  traverse_tile(s, ranges[tile], keys, vals, rec, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f, bl,
+                        neval, nmis);
+  // the replay must reproduce the forward blend count
+  const bool mismatch = in_image && bl.nblend != n_blended[p];
+  const unsigned ball = __ballot_sync(0xffffffffu, mismatch);
+  if ((threadIdx.x & 31) == 0 && ball) atomicAdd(&stats[kStatReplayMismatch], (unsigned long long)__popc(ball));
+}
+
+// ---------------------------------------------------------------------------
+// K7
+// ---------------------------------------------------------------------------
+
+constexpr float kY00 = 0.28209479177387814f;
+constexpr float kY1 = 0.4886025119029199f;
+constexpr float kY2a = 1.0925484305920792f;
+constexpr float kY2b = 0.31539156525252005f;
+constexpr float kY2c = 0.5462742152960396f;
+constexpr float kY3a = 0.5900435899266435f;
+constexpr float kY3b = 2.890611442640554f;
+constexpr float kY3c = 0.4570457994644658f;
+constexpr float kY3d = 0.3731763325901154f;
+constexpr float kY3e = 1.445305721320277f;
+
+// SH basis values Y[k] and their gradients dY[k] = dY_k/d(x,y,z) of the same
+// polynomials as the forward preprocess.
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int deg, float* Y, float3* dY) {
+  Y[0] = kY00;
+  dY[0] = f3(0.f, 0.f, 0.f);
+  if (deg < 1) return;
+  Y[1] = -kY1 * y;  dY[1] = f3(0.f, -kY1, 0.f);
+  Y[2] = kY1 * z;   dY[2] = f3(0.f, 0.f, kY1);
+  Y[3] = -kY1 * x;  dY[3] = f3(-kY1, 0.f, 0.f);
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kY2a * x * y;                 dY[4] = f3(kY2a * y, kY2a * x, 0.f);
+  Y[5] = -kY2a * y * z;                dY[5] = f3(0.f, -kY2a * z, -kY2a * y);
+  Y[6] = kY2b * (2.f * zz - xx - yy);  dY[6] = f3(-2.f * kY2b * x, -2.f * kY2b * y, 4.f * kY2b * z);
+  Y[7] = -kY2a * x * z;                dY[7] = f3(-kY2a * z, 0.f, -kY2a * x);
+  Y[8] = kY2c * (xx - yy);             dY[8] = f3(2.f * kY2c * x, -2.f * kY2c * y, 0.f);
+  if (deg < 3) return;
+  Y[9] = -kY3a * y * (3.f * xx - yy);
+  dY[9] = f3(-6.f * kY3a * x * y, -kY3a * (3.f * xx - 3.f * yy), 0.f);
+  Y[10] = kY3b * x * y * z;
+  dY[10] = f3(kY3b * y * z, kY3b * x * z, kY3b * x * y);
+  Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+  dY[11] = f3(2.f * kY3c * x * y, -kY3c * (4.f * zz - xx - 3.f * yy), -8.f * kY3c * y * z);
+  Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  dY[12] = f3(-6.f * kY3d * x * z, -6.f * kY3d * y * z, kY3d * (6.f * zz - 3.f * xx - 3.f * yy));
+  Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+  dY[13] = f3(-kY3c * (4.f * zz - 3.f * xx - yy), 2.f * kY3c * x * y, -8.f * kY3c * x * z);
+  Y[14] = kY3e * z * (xx - yy);
+  dY[14] = f3(2.f * kY3e * x * z, -2.f * kY3e * y * z, kY3e * (xx - yy));
+  Y[15] = -kY3a * x * (xx - 3.f * yy);
+  dY[15] = f3(-kY3a * (3.f * xx - 3.f * yy), 6.f * kY3a * x * y, 0.f);
+}
+
+__global__ void __launch_bounds__(128)
+preprocess_backward_kernel(SceneDev s, FrameConst fc, const uint4* __restrict__ aux,
+                           const float4* __restrict__ grad, float* __restrict__ g_means,
+                           float* __restrict__ g_log_scales, float* __restrict__ g_quats,
+                           float* __restrict__ g_opacity, float* __restrict__ g_sh) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const int K = (s.sh_degree + 1) * (s.sh_degree + 1);
+  const uint4 a = aux[i];
+  float* gsh = g_sh + (size_t)i * K * 3;
+  if ((a.x & 0xffffu) > (a.y & 0xffffu)) {   // not visible: zero gradient
+    for (int j = 0; j < 3; ++j) g_means[3 * i + j] = g_log_scales[3 * i + j] = 0.0f;
+    for (int j = 0; j < 4; ++j) g_quats[4 * i + j] = 0.0f;
+    g_opacity[i] = 0.0f;
+    for (int j = 0; j < K * 3; ++j) gsh[j] = 0.0f;
+    return;
+  }
+  const float4 G1 = grad[4 * i + 0], G2 = grad[4 * i + 1], G3 = grad[4 * i + 2], G4 = grad[4 * i + 3];
+
+  // ---- forward recomputation
+  const float mu[3] = {s.means[3 * i], s.means[3 * i + 1], s.means[3 * i + 2]};
+  const float ls[3] = {s.log_scales[3 * i], s.log_scales[3 * i + 1], s.log_scales[3 * i + 2]};
+  const float4 q4 = reinterpret_cast<const float4*>(s.quats)[i];
+  const float logit = s.opacity_logits[i];
+  const float vtrain = s.vhat_train[i];
+  const float vz = fc.Rv[6] * mu[0] + fc.Rv[7] * mu[1] + fc.Rv[8] * mu[2] + fc.tv[2];
+  float sc[3], a2[3];
+  for (int j = 0; j < 3; ++j) {
+    sc[j] = expf(ls[j]);
+    a2[j] = sc[j] * sc[j];
+  }
+  const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+  const float qinv = rsqrtf(qn2);
+  const float qw = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
+  float R[9];
+  R[0] = 1.0f - 2.0f * (qy * qy + qz * qz);
+  R[1] = 2.0f * (qx * qy - qw * qz);
+  R[2] = 2.0f * (qx * qz + qw * qy);
+  R[3] = 2.0f * (qx * qy + qw * qz);
+  R[4] = 1.0f - 2.0f * (qx * qx + qz * qz);
+  R[5] = 2.0f * (qy * qz - qw * qx);
+  R[6] = 2.0f * (qx * qz - qw * qy);
+  R[7] = 2.0f * (qy * qz + qw * qx);
+  R[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
+  const float opac = 1.0f / (1.0f + expf(-logit));
+  float kv = 0.0f, veff = 0.0f;
+  bool view_branch = false;
+  if (!(fc.flags & AAAG_FLAG_NO_FILTER)) {
+    const float vhat = fc.fx / fmaxf(vz, fc.znear);
+    view_branch = vhat < vtrain;
+    veff = fminf(vtrain, vhat);
+    kv = fc.k / (veff * veff);
+  }
+  float b[3], sp[3];
+  for (int j = 0; j < 3; ++j) {
+    b[j] = a2[j] + kv;
+    sp[j] = sqrtf(b[j]);
+  }
+  const float df[3] = {mu[0] - fc.o[0], mu[1] - fc.o[1], mu[2] - fc.o[2]};
+  const float dist = sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
+  const float d[3] = {df[0] / dist, df[1] / dist, df[2] / dist};
+  float dp[3];
+  for (int j = 0; j < 3; ++j) dp[j] = R[j] * d[0] + R[3 + j] * d[1] + R[6 + j] * d[2];
+  float w[3], r[3];
+  for (int j = 0; j < 3; ++j) {
+    w[j] = dp[j] * dp[j] / b[j];
+    r[j] = a2[j] / b[j];
+  }
+  const float P = w[0] * r[1] * r[2] + w[1] * r[0] * r[2] + w[2] * r[0] * r[1];
+  const float Q = w[0] + w[1] + w[2];
+  const float phi2 = P / Q;
+  const float phi = sqrtf(phi2);
+
+  // ---- gradients
+  float gmu[3] = {0.f, 0.f, 0.f}, gR[9], gb[3] = {0.f, 0.f, 0.f}, ga2[3] = {0.f, 0.f, 0.f};
+  float gd[3] = {0.f, 0.f, 0.f};
+  for (int j = 0; j < 9; ++j) gR[j] = 0.0f;
+  // T_view rows: t_r = (A_r, mu_v,r), A = Rv R S', mu_v = Rv mu + tv
+  const float gA[9] = {G1.x, G1.y, G1.z, G2.x, G2.y, G2.z, G3.x, G3.y, G3.z};
+  const float gmv[3] = {G1.w, G2.w, G3.w};
+  for (int j = 0; j < 3; ++j) gmu[j] += fc.Rv[j] * gmv[0] + fc.Rv[3 + j] * gmv[1] + fc.Rv[6 + j] * gmv[2];
+  // dM = Rv^T dA, M = R diag(s')
+  for (int k = 0; k < 3; ++k) {
+    for (int j = 0; j < 3; ++j) {
+      const float gM = fc.Rv[k] * gA[j] + fc.Rv[3 + k] * gA[3 + j] + fc.Rv[6 + k] * gA[6 + j];
+      gR[3 * k + j] += gM * sp[j];
+      gb[j] += gM * R[3 * k + j] * 0.5f / sp[j];   // s' = sqrt(b)
+    }
+  }
+  // o_hat = o phi
+  const float goh = G4.w;
+  const float gopac = goh * phi;
+  const float gphi2 = goh * opac * 0.5f / phi;
+  const float gP = gphi2 / Q, gQ = -gphi2 * phi2 / Q;
+  const float gw[3] = {gP * r[1] * r[2] + gQ, gP * r[0] * r[2] + gQ, gP * r[0] * r[1] + gQ};
+  const float gr[3] = {gP * (w[1] * r[2] + w[2] * r[1]), gP * (w[0] * r[2] + w[2] * r[0]),
+                       gP * (w[0] * r[1] + w[1] * r[0])};
+  float gdp[3];
+  for (int j = 0; j < 3; ++j) {
+    gb[j] += -gw[j] * w[j] / b[j] - gr[j] * r[j] / b[j];
+    ga2[j] += gr[j] / b[j];
+    gdp[j] = gw[j] * 2.0f * dp[j] / b[j];
+  }
+  float gkv = 0.0f;
+  for (int j = 0; j < 3; ++j) {
+    ga2[j] += gb[j];
+    gkv += gb[j];
+  }
+  // d' = R^T d
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j) {
+      gR[3 * k + j] += d[k] * gdp[j];
+      gd[k] += R[3 * k + j] * gdp[j];
+    }
+  // colour: max(0, sum_k Y_k(d) sh_k + 0.5)
+  {
+    float Y[16];
+    float3 dY[16];
+    sh_basis_grad(d[0], d[1], d[2], s.sh_degree, Y, dY);
+    const float* shp = s.sh + (size_t)i * K * 3;
+    float raw[3] = {0.5f, 0.5f, 0.5f};
+    for (int k = 0; k < K; ++k)
+      for (int c = 0; c < 3; ++c) raw[c] += Y[k] * shp[3 * k + c];
+    const float gcol[3] = {raw[0] > 0.f ? G4.x : 0.f, raw[1] > 0.f ? G4.y : 0.f, raw[2] > 0.f ? G4.z : 0.f};
+    for (int k = 0; k < K; ++k) {
+      float gy = 0.0f;
+      for (int c = 0; c < 3; ++c) {
+        gsh[3 * k + c] = gcol[c] * Y[k];
+        gy += gcol[c] * shp[3 * k + c];
+      }
+      gd[0] += gy * dY[k].x;
+      gd[1] += gy * dY[k].y;
+      gd[2] += gy * dY[k].z;
+    }
+  }
+  // d = (mu - o) / |mu - o|
+  const float dd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+  for (int j = 0; j < 3; ++j) gmu[j] += (gd[j] - d[j] * dd) / dist;
+  // kv = k / v'^2, v' = fx / z on the view branch (z > znear)
+  if (view_branch && vz > fc.znear) {
+    const float gveff = -2.0f * kv / veff * gkv;
+    const float gvz = -veff / vz * gveff;          // d(fx/z)/dz = -(fx/z)/z
+    for (int j = 0; j < 3; ++j) gmu[j] += fc.Rv[6 + j] * gvz;
+  }
+  // s^2 = exp(2 log s)
+  for (int j = 0; j < 3; ++j) g_log_scales[3 * i + j] = 2.0f * a2[j] * ga2[j];
+  for (int j = 0; j < 3; ++j) g_means[3 * i + j] = gmu[j];
+  g_opacity[i] = gopac * opac * (1.0f - opac);
+  // R(q_hat) -> q_hat -> q
+  float gq[4];
+  gq[0] = -2.f * qz * gR[1] + 2.f * qy * gR[2] + 2.f * qz * gR[3] - 2.f * qx * gR[5] - 2.f * qy * gR[6] +
+          2.f * qx * gR[7];
+  gq[1] = 2.f * qy * gR[1] + 2.f * qz * gR[2] + 2.f * qy * gR[3] - 4.f * qx * gR[4] - 2.f * qw * gR[5] +
+          2.f * qz * gR[6] + 2.f * qw * gR[7] - 4.f * qx * gR[8];
+  gq[2] = -4.f * qy * gR[0] + 2.f * qx * gR[1] + 2.f * qw * gR[2] + 2.f * qx * gR[3] + 2.f * qz * gR[5] -
+          2.f * qw * gR[6] + 2.f * qz * gR[7] - 4.f * qy * gR[8];
+  gq[3] = -4.f * qz * gR[0] - 2.f * qw * gR[1] + 2.f * qx * gR[2] + 2.f * qw * gR[3] - 4.f * qz * gR[4] +
+          2.f * qy * gR[5] + 2.f * qx * gR[6] + 2.f * qy * gR[7];
+  const float qh[4] = {qw, qx, qy, qz};
+  const float proj = gq[0] * qh[0] + gq[1] * qh[1] + gq[2] * qh[2] + gq[3] * qh[3];
+  for (int j = 0; j < 4; ++j) g_quats[4 * i + j] = (gq[j] - qh[j] * proj) * qinv;
+}
+
+}  // namespace
+
+aaag_status launch_render_backward(const SceneDev& s, aaag_workspace* ws, const float* rgb, const float* drgb,
+                                   const float* dalpha, const aaag_grads* out, cudaStream_t st) {
+  if (cudaMemsetAsync(ws->grad_acc, 0, (size_t)ws->n * sizeof(float4) * 4, st) != cudaSuccess)
+    return check_launch("backward memset");
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(render_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kTileSmemBytes);
+    configured = true;
+  }
+  const int alt = ws->sorted_in_alt;
+  render_backward_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kTileSmemBytes, st>>>(
+      ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->fc, rgb, drgb, dalpha, ws->final_T,
+      ws->n_blended, ws->grad_acc, ws->stats);
+  aaag_status e = check_launch("render_backward");
+  if (e != AAAG_OK || s.n == 0) return e;
+  const unsigned blocks = (unsigned)((s.n + 127) / 128);
+  preprocess_backward_kernel<<<blocks, 128, 0, st>>>(s, ws->fc, ws->aux, ws->grad_acc, out->means,
+                                                     out->log_scales, out->quats, out->opacity_logits, out->sh);
+  return check_launch("preprocess_backward");
+}
+
+}  // namespace aaag

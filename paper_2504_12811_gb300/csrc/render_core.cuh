@@ -1,0 +1,212 @@
+// Per-tile traversal shared by the forward render (K5) and its backward (K6).
+//
+// Both kernels walk a tile's sorted pairs with identical arithmetic (explicit
+// fmaf everywhere, so the two compile to the same rounding), the same
+// per-pixel re-sort queue and the same release rule; they differ only in what
+// happens when a contributor is blended, which is a functor.  The backward
+// pass therefore replays exactly the blend sequence of the forward pass.
+//
+// Plane form (paper Sec. 3.1, Eq. 4-5): with t_i the rows of T_view and tile
+// origin (x_t, y_t), U = fx t1 + (cx - x_t) t3 and W = fy t2 + (cy - y_t) t3.
+// For the tile-relative pixel centre (x, y) the transformed planes are
+// (n1, h1) = U - x t3 and (n2, h2) = W - y t3, and
+//     num = h1 n2 - h2 n1 = N0 + x Nx + y Ny,     d = n1 x n2 = D0 + x Dx + y Dy
+// (the xy terms cancel).  rho^2 = |num|^2 / |d|^2 is the squared distance of
+// the ray to the Gaussian's centre in its normalised space.  d is parallel to
+// the ray direction in Gaussian space, d = fx fy det(A) A^-1 r, so the view
+// depth of the maximum is t* = G.d / |d|^2 with G = fx fy adj(A) mu_v.
+//
+// Per-pixel order.  Pairs arrive sorted by key; the key of pair k+1, L_{k+1},
+// is a lower bound of the t* of every contributor arriving after pair k.  When
+// pair k contributes with depth t:
+//   1. queued entries with depth <= t and < L_{k+1} are blended (in order);
+//   2. if t < L_{k+1} the new contributor is blended at once, followed by the
+//      queued entries below L_{k+1}: nothing later can precede any of them;
+//   3. otherwise it is inserted into the pixel's sorted queue.
+// The result is the exact (t*, arrival) order as long as the queue does not
+// overflow; on overflow the nearer of the queue front and the new entry is
+// blended early and counted as a potential misorder.  The queue is a per-thread
+// ring buffer in shared memory laid out [slot][thread] (bank-conflict free):
+// O(1) pop, insertion by shifting from the tail.
+#pragma once
+
+#include "aaag_internal.cuh"
+
+namespace aaag {
+
+constexpr int kQueue = 16;   // per-pixel re-sort queue entries (power of two)
+
+struct TileSmem {
+  float4 a[kTilePixels];  // N0.xyz, o_hat
+  float4 b[kTilePixels];  // Nx.xyz, L_next: lower bound of t* for every later pair
+  float4 c[kTilePixels];  // Ny.xyz, Gaussian index (bits)
+  float4 d[kTilePixels];  // D0.xyz, G.x
+  float4 e[kTilePixels];  // Dx.xyz, G.y
+  float4 f[kTilePixels];  // Dy.xyz, G.z
+  float qt[kQueue][kTilePixels];     // queued depth t*
+  float qa[kQueue][kTilePixels];     // queued alpha
+  uint32_t qg[kQueue][kTilePixels];  // queued Gaussian index
+};
+constexpr size_t kTileSmemBytes = sizeof(TileSmem);
+
+__device__ __forceinline__ float decode_depth(uint32_t key, const FrameConst& fc) {
+  const uint32_t dk = key & ((fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u));
+  return __uint_as_float((dk << fc.depth_shift) + fc.znear_bits);
+}
+
+__device__ __forceinline__ float3 fma3(float s, float3 a, float3 b) {   // s a + b
+  return f3(fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z));
+}
+__device__ __forceinline__ float3 crs(float3 a, float3 b) {
+  return f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
+}
+
+// Coefficients of one Gaussian for one tile (cxm = cx - x_t, cym = cy - y_t).
+__device__ __forceinline__ void stage_one(TileSmem& s, int slot, const Record* rec, uint32_t gid, float Lnext,
+                                          const FrameConst& fc, float cxm, float cym) {
+  const float4* r = reinterpret_cast<const float4*>(rec + gid);
+  const float4 t1 = __ldg(r + 0), t2 = __ldg(r + 1), t3 = __ldg(r + 2), cw = __ldg(r + 3);
+  const float3 T3 = f3(t3.x, t3.y, t3.z);
+  const float3 Uv = fma3(cxm, T3, fc.fx * f3(t1.x, t1.y, t1.z));
+  const float Uw = fmaf(cxm, t3.w, fc.fx * t1.w);
+  const float3 Wv = fma3(cym, T3, fc.fy * f3(t2.x, t2.y, t2.z));
+  const float Ww = fmaf(cym, t3.w, fc.fy * t2.w);
+  const float3 N0 = fma3(Uw, Wv, -Ww * Uv);
+  const float3 Nx = fma3(Ww, T3, -t3.w * Wv);
+  const float3 Ny = fma3(t3.w, Uv, -Uw * T3);
+  const float3 D0 = crs(Uv, Wv);
+  const float3 Dx = crs(Wv, T3);
+  const float3 Dy = crs(T3, Uv);
+  const float3 A1 = f3(t1.x, t1.y, t1.z), A2 = f3(t2.x, t2.y, t2.z);
+  const float fxfy = fc.fx * fc.fy;
+  const float3 G = fxfy * fma3(t1.w, crs(A2, T3), fma3(t2.w, crs(T3, A1), t3.w * crs(A1, A2)));
+  s.a[slot] = make_float4(N0.x, N0.y, N0.z, cw.w);
+  s.b[slot] = make_float4(Nx.x, Nx.y, Nx.z, Lnext);
+  s.c[slot] = make_float4(Ny.x, Ny.y, Ny.z, __uint_as_float(gid));
+  s.d[slot] = make_float4(D0.x, D0.y, D0.z, G.x);
+  s.e[slot] = make_float4(Dx.x, Dx.y, Dx.z, G.y);
+  s.f[slot] = make_float4(Dy.x, Dy.y, Dy.z, G.z);
+}
+
+// Per-thread sorted ring buffer in shared memory.
+struct SmemQueue {
+  TileSmem* s;
+  int tid, head, n;
+  __device__ __forceinline__ int slot(int i) const { return (head + i) & (kQueue - 1); }
+  __device__ __forceinline__ float front_t() const { return s->qt[head][tid]; }
+  __device__ __forceinline__ float front_a() const { return s->qa[head][tid]; }
+  __device__ __forceinline__ uint32_t front_g() const { return s->qg[head][tid]; }
+  __device__ __forceinline__ void pop() {
+    head = (head + 1) & (kQueue - 1);
+    --n;
+  }
+  // sorted insert (n < kQueue); ties keep arrival order
+  __device__ __forceinline__ void insert(float t, float a, uint32_t g) {
+    int i = n;
+    while (i > 0) {
+      const int p = slot(i - 1);
+      const float tp = s->qt[p][tid];
+      if (!(tp > t)) break;
+      const int q = slot(i);
+      s->qt[q][tid] = tp;
+      s->qa[q][tid] = s->qa[p][tid];
+      s->qg[q][tid] = s->qg[p][tid];
+      --i;
+    }
+    const int q = slot(i);
+    s->qt[q][tid] = t;
+    s->qa[q][tid] = a;
+    s->qg[q][tid] = g;
+    ++n;
+  }
+};
+
+// Traverse one tile for one pixel.  Blender must provide:
+//   bool done;                                  pixel finished
+//   void blend(float alpha, uint32_t gid);      blend one contributor (may set done)
+template <class Blender>
+__device__ __forceinline__ void traverse_tile(TileSmem& s, const uint2 range, const uint32_t* __restrict__ keys,
+                                              const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
+                                              const FrameConst& fc, int tile_x, int tile_y, float x, float y,
+                                              Blender& bl, unsigned long long& neval, uint32_t& nmis) {
+  const float cxm = fc.cx - (float)(tile_x * kTile), cym = fc.cy - (float)(tile_y * kTile);
+  const float kInf = __int_as_float(0x7f800000);
+  SmemQueue q;
+  q.s = &s;
+  q.tid = threadIdx.x;
+  q.head = 0;
+  q.n = 0;
+  for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
+    if (__syncthreads_count(bl.done) == kTilePixels) break;
+    const uint32_t j = b0 + threadIdx.x;
+    if (j < range.y) {
+      const float Lnext = j + 1 < range.y ? decode_depth(keys[j + 1], fc) : kInf;
+      stage_one(s, threadIdx.x, rec, vals[j], Lnext, fc, cxm, cym);
+    }
+    __syncthreads();
+    const int cnt = (int)min((uint32_t)kTilePixels, range.y - b0);
+    if (!bl.done) {
+      neval += (unsigned long long)cnt;
+      for (int k = 0; k < cnt; ++k) {
+        const float4 a = s.a[k], bq = s.b[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
+        const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
+        const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
+        const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
+        const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
+        const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
+        const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
+        const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
+        const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+        const float inv = __fdividef(1.0f, dd);
+        const float rho2 = nn * inv;
+        const float raw = a.w * __expf(-0.5f * rho2);
+        if (raw >= kAlphaMin) {
+          const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
+          if (ts >= fc.znear) {
+            const float Lnext = bq.w;
+            const float ca = fminf(raw, kAlphaMax);
+            const uint32_t cg = __float_as_uint(c.w);
+            // 1. queued entries in front of the new one that nothing later can precede
+            while (q.n > 0 && !bl.done) {
+              const float ft = q.front_t();
+              if (!(ft <= ts && ft < Lnext)) break;
+              bl.blend(q.front_a(), q.front_g());
+              q.pop();
+            }
+            if (bl.done) break;
+            if (ts < Lnext) {
+              // 2. the new contributor, then the rest below L_next
+              bl.blend(ca, cg);
+              while (q.n > 0 && !bl.done && q.front_t() < Lnext) {
+                bl.blend(q.front_a(), q.front_g());
+                q.pop();
+              }
+              if (bl.done) break;
+            } else {
+              // 3. queue it
+              if (q.n == kQueue) {
+                ++nmis;
+                if (ts < q.front_t()) {
+                  bl.blend(ca, cg);
+                  if (bl.done) break;
+                  continue;
+                }
+                bl.blend(q.front_a(), q.front_g());
+                q.pop();
+                if (bl.done) break;
+              }
+              q.insert(ts, ca, cg);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  while (q.n > 0 && !bl.done) {
+    bl.blend(q.front_a(), q.front_g());
+    q.pop();
+  }
+}
+
+}  // namespace aaag
