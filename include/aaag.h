@@ -258,6 +258,31 @@ aaag_status aaag_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                             int32_t* result_in_alt, cudaStream_t stream);
 
 /* --------------------------------------------------------------------------
+ * aaag_radix_sort_static -- the same stable radix sort for callers that
+ * cannot allocate device memory: a plug-in inside a host application that
+ * owns every device allocation, or a real-time loop that must not wait on the
+ * allocator or fragment its pool.  (This entry point has no counterpart in
+ * the paper; it is an interface convenience.)  It sorts keys[0..n) in place
+ * (low `key_bits` bits significant, 1..32) and carries vals along; the caller
+ * passes only these two device arrays.  Every other buffer (ping-pong copies,
+ * histograms, look-back words) lives in one fixed device array inside the
+ * library, sized for aaag_radix_sort_static_capacity() = 2^20 keys (about
+ * 8.5 MB, held by every GPU that loads the library until the process exits).
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ * The first call on a device resolves that array's address (once per
+ * device, with the device current), so make the first call before any stream
+ * capture.  All calls share the array: two calls that overlap on the GPU
+ * (different streams, or different threads without ordering) race and give
+ * wrong results; order them on one stream.  A look-back wait that gives up
+ * leaves the output unspecified (no trap, no hang).
+ * Errors: INVALID_ARG (n < 0, key_bits out of range, null arrays),
+ * CAPACITY (n > capacity), CUDA.
+ * ------------------------------------------------------------------------ */
+int64_t aaag_radix_sort_static_capacity(void);
+aaag_status aaag_radix_sort_static(uint32_t* keys, uint32_t* vals, int64_t n,
+                                   int32_t key_bits, cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
  * aaag_get_stats -- synchronises `stream` and copies the frame statistics to
  * *out (host).  Returns CAPACITY if the pair capacity overflowed, TIMEOUT if a
  * bounded device wait gave up, else OK.

@@ -84,6 +84,8 @@ SIGNATURES = [
     ("aaag_radix_sort_scratch_bytes", C.c_size_t, [C.c_int64]),
     ("aaag_radix_sort", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                   C.c_void_p, C.c_size_t, C.POINTER(C.c_int32), C.c_void_p]),
+    ("aaag_radix_sort_static_capacity", C.c_int64, []),
+    ("aaag_radix_sort_static", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
     ("aaag_get_stats", C.c_int, [C.c_void_p, C.POINTER(aaag_stats), C.c_void_p]),
     ("aaag_last_error", C.c_char_p, []),
 ]
@@ -175,6 +177,14 @@ def aaag_radix_sort(keys, vals, keys_alt, vals_alt, n, key_bits, scratch, scratc
     _check(lib().aaag_radix_sort(keys, vals, keys_alt, vals_alt, n, key_bits, scratch, scratch_bytes,
                                  C.byref(alt), stream), "aaag_radix_sort")
     return int(alt.value)
+
+
+def aaag_radix_sort_static_capacity():
+    return int(lib().aaag_radix_sort_static_capacity())
+
+
+def aaag_radix_sort_static(keys, vals, n, key_bits, stream):
+    _check(lib().aaag_radix_sort_static(keys, vals, n, key_bits, stream), "aaag_radix_sort_static")
 
 
 def aaag_get_stats(ws, stream, check=True):
