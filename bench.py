@@ -29,7 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "1080p frames/s @1M Gaussians (fwd)"  # fwd+bwd reported under "fwd_bwd"
+METRIC = "1080p frames/s @1M Gaussians (fwd)"  # fwd+bwd under "fwd_bwd", served p50/p99 under "serving"
 WORKLOAD = "scene1m: 1,000,000 Gaussians (64 clusters + 10% shell, SH 3), 1920x1080, 16 poses"
 
 # algorithmic FP32 operations per pixel x Gaussian evaluation in the render
@@ -49,7 +49,49 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--capacity", type=int, default=48 << 20)
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="length of the Poisson serving trace (0 = skip serving)")
+    ap.add_argument("--serve-rate", type=float, default=400.0)
+    ap.add_argument("--serve-capacity", type=int, default=120 << 20)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     return ap.parse_args()
+
+
+def run_serving(args, dev):
+    """Served-request latency: the continuous-batching server against the
+    plain per-frame renderer, on the same Poisson trace of mixed requests over
+    three resident scenes."""
+    import numpy as np
+    import torch
+    from paper_2504_12811_gb300 import scenes, serve
+    t = time.time()
+    sc = scenes.serving_scenes()
+    trace = scenes.serving_trace(args.serve_rate, args.serve_seconds)
+    gen_s = time.time() - t
+    n_views = sum(len(r.cams) for r in trace)
+    server = serve.Server(sc, int(args.serve_budget_gb * 2**30), 1920, 1920, args.serve_capacity,
+                          max_batch_views=8, device=dev)
+    n_slots = len(server.slots)
+    try:
+        server.warm(trace)
+        t = time.time()
+        lat = server.serve(trace)
+        ours_wall = time.time() - t
+    finally:
+        server.close()
+    ours = serve.latency_summary(lat, max(ours_wall, args.serve_seconds), n_views)
+    del server
+    torch.cuda.empty_cache()
+    t = time.time()
+    lat_p = serve.plain_renderer(sc, trace, 1920, 1920, args.serve_capacity, device=dev)
+    plain_wall = time.time() - t
+    plain = serve.latency_summary(lat_p, max(plain_wall, args.serve_seconds), n_views)
+    return {"trace": {"rate_hz": args.serve_rate, "seconds": args.serve_seconds, "requests": len(trace),
+                      "views": n_views, "mix": "1/3 640x480 60deg, 1/3 1920x1080 60deg, 1/3 stereo 2x1832x1920 110deg",
+                      "scenes": {k: v.n for k, v in sc.items()}},
+            "server": dict(ours, slots=n_slots, budget_gb=args.serve_budget_gb, wall_s=ours_wall),
+            "plain_per_frame": dict(plain, wall_s=plain_wall),
+            "generation_s": gen_s}
 
 
 def dist_env():
@@ -365,6 +407,8 @@ def run_ours(args):
         "wall_s_timed": wall,
         "scene_generation_s": t_gen,
     }
+    if args.serve_seconds > 0:
+        line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, cores, frame_s = cpu_baseline(scene, poses, args.cpu_seconds, W * H)
         line["cpu_baseline"] = {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",

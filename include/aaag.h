@@ -124,7 +124,8 @@ typedef struct {
                             space -> view space; t_i = (A_i0,A_i1,A_i2,mu_v,i)),
                             then (r, g, b, o_hat)                            */
   uint32_t* aux;         /* [n][4]: tile rect (tx0 | ty0<<16, tx1 | ty1<<16),
-                            tau_rho bits, depth-key bits; empty rect
+                            tau_rho float bits (negated when the ellipsoid
+                            reaches znear), depth-key bits; empty rect
                             (tx0 > tx1) = not visible                         */
   uint32_t* counts;      /* [n] chunks of 32 candidate tiles per Gaussian    */
   uint32_t* offsets;     /* [n] exclusive prefix sum of counts               */
@@ -141,8 +142,9 @@ typedef struct {
 } aaag_workspace_view;
 
 /* --------------------------------------------------------------------------
- * Workspace.  Bytes needed for n Gaussians, a width x height image and up to
- * pair_capacity (tile, Gaussian) pairs.  The caller allocates that many bytes
+ * Workspace.  Bytes needed for up to n Gaussians, images up to width x height
+ * and up to pair_capacity (tile, Gaussian) pairs; any smaller scene or image
+ * can be rendered with it.  The caller allocates that many bytes
  * of device memory (256-byte aligned) and keeps them alive while the
  * workspace is used; _init writes a small host-side descriptor to *ws
  * (malloc'd; release with _destroy, which never frees dev_mem).
@@ -169,9 +171,10 @@ aaag_status aaag_workspace_get_view(const aaag_workspace* ws,
  *   view-space angular bounds of Eq. 14-17 -> tile rectangle; cull against
  *   the whole image frustum truncated at znear (Eq. 18 over the image);
  *   SH colour; depth key from the front of the tau-ellipsoid.
- * Reads scene arrays; writes the workspace records (n must equal the n the
- * workspace was created for, width/height likewise).  Resets the frame
- * statistics.
+ * Reads scene arrays; writes the workspace records.  scene->n, width and
+ * height may be anything up to the workspace's maxima.  The frame constants
+ * (camera, tiling, key layout) go to device memory through one single-thread
+ * kernel, the first launch of the frame.  Resets the frame statistics.
  * Errors: INVALID_ARG, UNSUPPORTED (sh_degree > 3), CUDA.
  * ------------------------------------------------------------------------ */
 aaag_status aaag_preprocess(const aaag_scene* scene /* host struct */,
@@ -241,6 +244,43 @@ aaag_status aaag_render_backward(const aaag_scene* scene /* host struct */,
 aaag_status aaag_render_frame(const aaag_scene* scene, const aaag_camera* camera,
                               const aaag_params* params, aaag_workspace* ws,
                               float* rgb, float* alpha, cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
+ * aaag_render_batch -- the render of aaag_render for n frames (1..64) at once,
+ * as one persistent launch whose blocks take (frame, tile) work items from a
+ * shared counter (a serving form of Sec. 3.1 rendering: tiles of small and
+ * large frames interleave on the GPU).  Each workspace must hold a sorted
+ * frame (aaag_sort, possibly issued on other streams: order them before this
+ * call, e.g. with events).  rgb[i], alpha[i] are device outputs of frame i
+ * (layout of aaag_render).  Host arrays of n pointers.  Per-frame results are
+ * identical to aaag_render's.  Errors: INVALID_ARG, CUDA.
+ * ------------------------------------------------------------------------ */
+aaag_status aaag_render_batch(aaag_workspace* const* ws, float* const* rgb,
+                              float* const* alpha, int32_t n, cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
+ * Frame graphs.  aaag_graph_create captures the listed stages of one frame
+ * (AAAG_STAGE_PREPROCESS must be among them) for a fixed scene, workspace,
+ * image size and parameters into a CUDA graph on `stream` (a non-default
+ * stream; the stages are recorded, not run).  aaag_graph_launch runs it for
+ * any camera of the same image size: only the first node, the one that writes
+ * the frame constants to device memory, is re-parameterised.  The workspace
+ * then holds that frame as if the stages had been called one by one.  A graph
+ * is host memory (release with aaag_graph_destroy); device memory is still only
+ * the caller's.  Errors: INVALID_ARG, CUDA (capture or instantiation failed).
+ * ------------------------------------------------------------------------ */
+#define AAAG_STAGE_PREPROCESS 1
+#define AAAG_STAGE_CULL       2
+#define AAAG_STAGE_SORT       4
+#define AAAG_STAGE_RENDER     8
+typedef struct aaag_graph aaag_graph;
+aaag_status aaag_graph_create(const aaag_scene* scene, const aaag_camera* camera,
+                              const aaag_params* params, aaag_workspace* ws,
+                              int32_t stages, float* rgb, float* alpha,
+                              cudaStream_t stream, aaag_graph** out);
+aaag_status aaag_graph_launch(aaag_graph* g, const aaag_camera* camera,
+                              cudaStream_t stream);
+void aaag_graph_destroy(aaag_graph* g);
 
 /* --------------------------------------------------------------------------
  * aaag_radix_sort -- the stable LSD radix sort used by aaag_sort, on caller

@@ -18,6 +18,7 @@ AAAG_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CAPACITY", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED"}
 AAAG_FLAG_NO_FILTER = 1
 AAAG_FLAG_NO_CULL = 2
+AAAG_STAGE_PREPROCESS, AAAG_STAGE_CULL, AAAG_STAGE_SORT, AAAG_STAGE_RENDER = 1, 2, 4, 8
 
 
 class AaagError(RuntimeError):
@@ -81,6 +82,13 @@ SIGNATURES = [
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("aaag_render_backward", C.c_int, [C.POINTER(aaag_scene), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.POINTER(aaag_grads), C.c_void_p]),
+    ("aaag_render_batch", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                    C.c_int32, C.c_void_p]),
+    ("aaag_graph_create", C.c_int, [C.POINTER(aaag_scene), C.POINTER(aaag_camera), C.POINTER(aaag_params),
+                                    C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.POINTER(C.c_void_p)]),
+    ("aaag_graph_launch", C.c_int, [C.c_void_p, C.POINTER(aaag_camera), C.c_void_p]),
+    ("aaag_graph_destroy", None, [C.c_void_p]),
     ("aaag_radix_sort_scratch_bytes", C.c_size_t, [C.c_int64]),
     ("aaag_radix_sort", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                   C.c_void_p, C.c_size_t, C.POINTER(C.c_int32), C.c_void_p]),
@@ -166,6 +174,30 @@ def aaag_render_frame(scene, camera, params, ws, rgb_ptr, alpha_ptr, stream):
 def aaag_render_backward(scene, ws, rgb_ptr, drgb_ptr, dalpha_ptr, grads, stream):
     _check(lib().aaag_render_backward(C.byref(scene), ws, rgb_ptr, drgb_ptr, dalpha_ptr, C.byref(grads), stream),
            "aaag_render_backward")
+
+
+def aaag_render_batch(ws_handles, rgb_ptrs, alpha_ptrs, stream):
+    n = len(ws_handles)
+    W = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in ws_handles])
+    R = (C.c_void_p * n)(*rgb_ptrs)
+    A = (C.c_void_p * n)(*alpha_ptrs)
+    _check(lib().aaag_render_batch(W, R, A, n, stream), "aaag_render_batch")
+
+
+def aaag_graph_create(scene, camera, params, ws, stages, rgb_ptr, alpha_ptr, stream):
+    out = C.c_void_p()
+    _check(lib().aaag_graph_create(C.byref(scene), C.byref(camera),
+                                   C.byref(params) if params is not None else None, ws, stages,
+                                   rgb_ptr, alpha_ptr, stream, C.byref(out)), "aaag_graph_create")
+    return out
+
+
+def aaag_graph_launch(graph, camera, stream):
+    _check(lib().aaag_graph_launch(graph, C.byref(camera), stream), "aaag_graph_launch")
+
+
+def aaag_graph_destroy(graph):
+    lib().aaag_graph_destroy(graph)
 
 
 def aaag_radix_sort_scratch_bytes(n):

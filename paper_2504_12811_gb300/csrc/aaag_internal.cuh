@@ -69,6 +69,7 @@ enum StatSlot : int {
   kStatSortEpoch = 8,
   kStatChunks = 9,         // chunks of 32 candidate tiles (K2 work items)
   kStatReplayMismatch = 10,// pixels whose backward replay blended a different count
+  kStatBatchCounter = 11,  // uint32 work-item counter of the batched render
   kStatChunksClipped = 14, // uint32: chunk count clipped to the chunk capacity
   kStatPairsClipped = 15,  // uint32: pair count clipped to the pair capacity
   kStatCount = 16
@@ -78,6 +79,10 @@ enum StatSlot : int {
 
 // Host-side workspace descriptor.
 struct aaag_workspace {
+  // capacity fixed at init
+  int64_t n_max;
+  int width_max, height_max, n_tiles_max;
+  // current frame (set by aaag_preprocess)
   int64_t n;
   int width, height, tiles_x, tiles_y, n_tiles;
   int64_t capacity;
@@ -102,7 +107,8 @@ struct aaag_workspace {
   uint32_t* n_blended;           // [H*W]
   unsigned long long* stats;     // [kStatCount]
   float4* grad_acc;              // [n][4] backward accumulators (dt1, dt2, dt3, colour + o_hat)
-  aaag::FrameConst fc;
+  aaag::FrameConst fc;            // host copy of the current frame constants
+  aaag::FrameConst* fc_dev;       // device copy read by the kernels
   bool have_frame;
   int sorted_in_alt;             // which buffer holds the sorted pairs
   int64_t n_scan_blocks;
@@ -122,6 +128,12 @@ aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_
 aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st);
+aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, float* const* alpha, int n,
+                                cudaStream_t st);
+void prepare_render_kernels();
+void prepare_backward_kernels();
+void prepare_sort_kernels();
+constexpr int kMaxRenderBatch = 64;
 aaag_status launch_render_backward(const SceneDev& s, aaag_workspace* ws, const float* rgb, const float* drgb,
                                    const float* dalpha, const aaag_grads* out, cudaStream_t st);
 aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,

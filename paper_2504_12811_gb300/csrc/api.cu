@@ -36,7 +36,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
   size_t records, aux, counts, offsets, partials, owner, mask, pofs, keys0, keys1, vals0, vals1, hist, counters,
-      lookback, ranges, final_T, n_blended, stats, grad, total;
+      lookback, ranges, final_T, n_blended, stats, grad, fc, total;
 };
 
 int tiles_of(int size) { return (size + kTile - 1) / kTile; }
@@ -77,6 +77,7 @@ Layout layout_of(int64_t n, int w, int h, int64_t cap) {
   L.n_blended = take((size_t)w * h * 4);
   L.stats = take(kStatCount * 8);
   L.grad = take((size_t)n * 64);
+  L.fc = take(sizeof(FrameConst));
   L.total = off;
   return L;
 }
@@ -149,6 +150,11 @@ aaag_status make_frame(const aaag_camera* cam, const aaag_params* prm, int sh_de
 
 __global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
 
+// Frame constants are a kernel parameter here and device memory for every
+// other kernel of the frame: a captured frame graph is re-aimed at a new
+// camera by updating this one node.
+__global__ void set_frame_kernel(FrameConst* dst, FrameConst v) { *dst = v; }
+
 SceneDev scene_dev(const aaag_scene* scene) {
   SceneDev s;
   s.n = scene->n;
@@ -162,8 +168,8 @@ SceneDev scene_dev(const aaag_scene* scene) {
   return s;
 }
 
-aaag_status check_scene(const aaag_scene* scene, const aaag_workspace* ws, const char* who) {
-  if (scene->n != ws->n) {
+aaag_status check_scene(const aaag_scene* scene, const aaag_workspace* ws, const char* who, bool same_frame) {
+  if (same_frame && scene->n != ws->n) {
     set_error("%s: scene has %lld Gaussians, the workspace %lld", who, (long long)scene->n, (long long)ws->n);
     return AAAG_ERR_INVALID_ARG;
   }
@@ -223,6 +229,10 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
     return AAAG_ERR_CAPACITY;
   }
   char* b = static_cast<char*>(dev_mem);
+  w->n_max = n;
+  w->width_max = width;
+  w->height_max = height;
+  w->n_tiles_max = tx * ty;
   w->n = n;
   w->width = width;
   w->height = height;
@@ -253,6 +263,7 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
   w->n_blended = reinterpret_cast<uint32_t*>(b + L.n_blended);
   w->stats = reinterpret_cast<unsigned long long*>(b + L.stats);
   w->grad_acc = reinterpret_cast<float4*>(b + L.grad);
+  w->fc_dev = reinterpret_cast<FrameConst*>(b + L.fc);
   w->n_scan_blocks = (n + 4095) / 4096;
   w->n_sort_tiles = (pair_capacity + kSortTileKeys - 1) / kSortTileKeys;
   // the look-back epoch lives in the stats block and must start defined; the
@@ -262,6 +273,11 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
     std::free(w);
     return check_launch("workspace_init memset");
   }
+  // function attributes and occupancy queries, once per process, outside any
+  // stream capture
+  prepare_render_kernels();
+  prepare_backward_kernels();
+  prepare_sort_kernels();
   *ws = w;
   return AAAG_OK;
 }
@@ -298,13 +314,15 @@ aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, 
     set_error("aaag_preprocess: null argument");
     return AAAG_ERR_INVALID_ARG;
   }
-  if (scene->n != ws->n || camera->width != ws->width || camera->height != ws->height) {
-    set_error("aaag_preprocess: scene/camera size (%lld, %dx%d) differs from the workspace (%lld, %dx%d)",
-              (long long)scene->n, camera->width, camera->height, (long long)ws->n, ws->width, ws->height);
+  if (scene->n < 0 || scene->n > ws->n_max || camera->width <= 0 || camera->height <= 0 ||
+      camera->width > ws->width_max || camera->height > ws->height_max) {
+    set_error("aaag_preprocess: scene/camera size (%lld, %dx%d) exceeds the workspace (%lld, %dx%d)",
+              (long long)scene->n, camera->width, camera->height, (long long)ws->n_max, ws->width_max,
+              ws->height_max);
     return AAAG_ERR_INVALID_ARG;
   }
   {
-    const aaag_status e = check_scene(scene, ws, "aaag_preprocess");
+    const aaag_status e = check_scene(scene, ws, "aaag_preprocess", false);
     if (e != AAAG_OK) return e;
   }
   if (!finite_camera(camera)) {
@@ -315,6 +333,13 @@ aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, 
     set_error("aaag_preprocess: params out of range");
     return AAAG_ERR_INVALID_ARG;
   }
+  // frame dimensions (at most the workspace's)
+  ws->n = scene->n;
+  ws->width = camera->width;
+  ws->height = camera->height;
+  ws->tiles_x = tiles_of(camera->width);
+  ws->tiles_y = tiles_of(camera->height);
+  ws->n_tiles = ws->tiles_x * ws->tiles_y;
   FrameConst fc;
   std::memset(&fc, 0, sizeof(fc));
   aaag_status e = make_frame(camera, params, scene->sh_degree, ws, &fc);
@@ -322,6 +347,9 @@ aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, 
   ws->fc = fc;
   ws->have_frame = true;
   ws->sorted_in_alt = 0;
+  set_frame_kernel<<<1, 1, 0, stream>>>(ws->fc_dev, fc);
+  e = check_launch("set_frame");
+  if (e != AAAG_OK) return e;
   // reset per-frame statistics (keep the sort epoch)
   if (cudaMemsetAsync(ws->stats, 0, kStatSortEpoch * 8, stream) != cudaSuccess)
     return check_launch("preprocess memset");
@@ -368,7 +396,7 @@ aaag_status aaag_render_backward(const aaag_scene* scene, aaag_workspace* ws, co
     set_error("aaag_render_backward: null argument or no rendered frame");
     return AAAG_ERR_INVALID_ARG;
   }
-  aaag_status e = check_scene(scene, ws, "aaag_render_backward");
+  aaag_status e = check_scene(scene, ws, "aaag_render_backward", true);
   if (e != AAAG_OK) return e;
   if (scene->sh_degree != ws->fc.sh_degree) {
     set_error("aaag_render_backward: scene differs from the preprocessed one");
@@ -452,6 +480,158 @@ aaag_status aaag_get_stats(aaag_workspace* ws, aaag_stats* out, cudaStream_t str
     return AAAG_ERR_TIMEOUT;
   }
   return AAAG_OK;
+}
+
+aaag_status aaag_render_batch(aaag_workspace* const* ws, float* const* rgb, float* const* alpha, int32_t n,
+                              cudaStream_t stream) {
+  if (!ws || !rgb || !alpha || n < 1 || n > kMaxRenderBatch) {
+    set_error("aaag_render_batch: need 1..%d frames", kMaxRenderBatch);
+    return AAAG_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!ws[i] || !ws[i]->have_frame || !rgb[i] || !alpha[i]) {
+      set_error("aaag_render_batch: frame %d has no workspace, no sorted pairs or no output", i);
+      return AAAG_ERR_INVALID_ARG;
+    }
+  }
+  return launch_render_batch(ws, rgb, alpha, n, stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// frame graphs
+// ---------------------------------------------------------------------------
+
+struct aaag_graph {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  cudaGraphNode_t frame_node;
+  cudaKernelNodeParams frame_params;
+  aaag_workspace* ws;
+  aaag_params params;
+  bool has_params;
+  int sh_degree, width, height, stages;
+};
+
+extern "C" {
+
+aaag_status aaag_graph_create(const aaag_scene* scene, const aaag_camera* camera, const aaag_params* params,
+                              aaag_workspace* ws, int32_t stages, float* rgb, float* alpha, cudaStream_t stream,
+                              aaag_graph** out) {
+  if (!scene || !camera || !ws || !out || !(stages & AAAG_STAGE_PREPROCESS) || (stages & ~15) ||
+      ((stages & AAAG_STAGE_RENDER) && (!rgb || !alpha))) {
+    set_error("aaag_graph_create: invalid argument");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (!stream) {
+    set_error("aaag_graph_create: capture needs a non-default stream");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return check_launch("aaag_graph_create begin capture");
+  aaag_status e = aaag_preprocess(scene, camera, params, ws, stream);
+  if (e == AAAG_OK && (stages & AAAG_STAGE_CULL)) e = aaag_cull(ws, stream);
+  if (e == AAAG_OK && (stages & AAAG_STAGE_SORT)) e = aaag_sort(ws, stream);
+  if (e == AAAG_OK && (stages & AAAG_STAGE_RENDER)) e = aaag_render(ws, rgb, alpha, stream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(stream, &graph);
+  if (e != AAAG_OK || ce != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    if (e == AAAG_OK) {
+      set_error("aaag_graph_create: capture failed: %s", cudaGetErrorString(ce));
+      e = AAAG_ERR_CUDA;
+    }
+    cudaGetLastError();
+    return e;
+  }
+  // the frame-constant node
+  size_t count = 0;
+  cudaGraphGetNodes(graph, nullptr, &count);
+  cudaGraphNode_t* nodes = static_cast<cudaGraphNode_t*>(std::calloc(count ? count : 1, sizeof(cudaGraphNode_t)));
+  cudaGraphGetNodes(graph, nodes, &count);
+  cudaGraphNode_t frame_node = nullptr;
+  cudaKernelNodeParams fp;
+  std::memset(&fp, 0, sizeof(fp));
+  for (size_t i = 0; i < count && !frame_node; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams p;
+    if (cudaGraphKernelNodeGetParams(nodes[i], &p) == cudaSuccess &&
+        p.func == reinterpret_cast<void*>(set_frame_kernel)) {
+      frame_node = nodes[i];
+      fp = p;
+    }
+  }
+  std::free(nodes);
+  cudaGraphExec_t exec = nullptr;
+  if (!frame_node || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    set_error("aaag_graph_create: %s", frame_node ? "instantiation failed" : "frame node not found");
+    cudaGetLastError();
+    return AAAG_ERR_CUDA;
+  }
+  auto* g = static_cast<aaag_graph*>(std::calloc(1, sizeof(aaag_graph)));
+  if (!g) {
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    set_error("aaag_graph_create: out of host memory");
+    return AAAG_ERR_CAPACITY;
+  }
+  g->graph = graph;
+  g->exec = exec;
+  g->frame_node = frame_node;
+  g->frame_params = fp;
+  g->ws = ws;
+  g->has_params = params != nullptr;
+  if (params) g->params = *params;
+  g->sh_degree = scene->sh_degree;
+  g->width = camera->width;
+  g->height = camera->height;
+  g->stages = stages;
+  *out = g;
+  return AAAG_OK;
+}
+
+aaag_status aaag_graph_launch(aaag_graph* g, const aaag_camera* camera, cudaStream_t stream) {
+  if (!g || !camera) {
+    set_error("aaag_graph_launch: null argument");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (camera->width != g->width || camera->height != g->height || !finite_camera(camera)) {
+    set_error("aaag_graph_launch: camera must be finite and %dx%d like the captured frame", g->width, g->height);
+    return AAAG_ERR_INVALID_ARG;
+  }
+  aaag_workspace* ws = g->ws;
+  // the workspace dimensions are those of the captured frame
+  ws->width = g->width;
+  ws->height = g->height;
+  ws->tiles_x = tiles_of(g->width);
+  ws->tiles_y = tiles_of(g->height);
+  ws->n_tiles = ws->tiles_x * ws->tiles_y;
+  FrameConst fc;
+  std::memset(&fc, 0, sizeof(fc));
+  aaag_status e = make_frame(camera, g->has_params ? &g->params : nullptr, g->sh_degree, ws, &fc);
+  if (e != AAAG_OK) return e;
+  FrameConst* dst = ws->fc_dev;
+  void* args[2] = {&dst, &fc};
+  cudaKernelNodeParams p = g->frame_params;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  if (cudaGraphExecKernelNodeSetParams(g->exec, g->frame_node, &p) != cudaSuccess)
+    return check_launch("aaag_graph_launch update");
+  if (cudaGraphLaunch(g->exec, stream) != cudaSuccess) return check_launch("aaag_graph_launch");
+  ws->fc = fc;
+  ws->have_frame = true;
+  ws->sorted_in_alt = 0;
+  return AAAG_OK;
+}
+
+void aaag_graph_destroy(aaag_graph* g) {
+  if (!g) return;
+  cudaGraphExecDestroy(g->exec);
+  cudaGraphDestroy(g->graph);
+  std::free(g);
 }
 
 }  // extern "C"

@@ -99,13 +99,14 @@ struct BackwardBlend {
 
 __global__ void __launch_bounds__(kTilePixels, 2)
 render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
-                       const uint32_t* __restrict__ vals, const Record* __restrict__ rec, FrameConst fc,
-                       const float* __restrict__ rgb, const float* __restrict__ drgb,
+                       const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
+                       const FrameConst* __restrict__ fcp, const float* __restrict__ rgb, const float* __restrict__ drgb,
                        const float* __restrict__ dalpha, const float* __restrict__ final_T,
                        const uint32_t* __restrict__ n_blended, float4* __restrict__ grad,
                        unsigned long long* __restrict__ stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileSmem& s = *reinterpret_cast<TileSmem*>(smem_raw);
+  const FrameConst fc = *fcp;
   const int tile = blockIdx.x;
   const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
   const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
@@ -199,12 +200,13 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int deg
 }
 
 __global__ void __launch_bounds__(128)
-preprocess_backward_kernel(SceneDev s, FrameConst fc, const uint4* __restrict__ aux,
+preprocess_backward_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const uint4* __restrict__ aux,
                            const float4* __restrict__ grad, float* __restrict__ g_means,
                            float* __restrict__ g_log_scales, float* __restrict__ g_quats,
                            float* __restrict__ g_opacity, float* __restrict__ g_sh) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s.n) return;
+  const FrameConst fc = *fcp;
   const int K = (s.sh_degree + 1) * (s.sh_degree + 1);
   const uint4 a = aux[i];
   float* gsh = g_sh + (size_t)i * K * 3;
@@ -363,24 +365,26 @@ preprocess_backward_kernel(SceneDev s, FrameConst fc, const uint4* __restrict__ 
 
 }  // namespace
 
+void prepare_backward_kernels() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(render_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+  done = true;
+}
+
 aaag_status launch_render_backward(const SceneDev& s, aaag_workspace* ws, const float* rgb, const float* drgb,
                                    const float* dalpha, const aaag_grads* out, cudaStream_t st) {
   if (cudaMemsetAsync(ws->grad_acc, 0, (size_t)ws->n * sizeof(float4) * 4, st) != cudaSuccess)
     return check_launch("backward memset");
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(render_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kTileSmemBytes);
-    configured = true;
-  }
+  prepare_backward_kernels();
   const int alt = ws->sorted_in_alt;
   render_backward_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kTileSmemBytes, st>>>(
-      ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->fc, rgb, drgb, dalpha, ws->final_T,
+      ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->fc_dev, rgb, drgb, dalpha, ws->final_T,
       ws->n_blended, ws->grad_acc, ws->stats);
   aaag_status e = check_launch("render_backward");
   if (e != AAAG_OK || s.n == 0) return e;
   const unsigned blocks = (unsigned)((s.n + 127) / 128);
-  preprocess_backward_kernel<<<blocks, 128, 0, st>>>(s, ws->fc, ws->aux, ws->grad_acc, out->means,
+  preprocess_backward_kernel<<<blocks, 128, 0, st>>>(s, ws->fc_dev, ws->aux, ws->grad_acc, out->means,
                                                      out->log_scales, out->quats, out->opacity_logits, out->sh);
   return check_launch("preprocess_backward");
 }

@@ -186,10 +186,11 @@ __device__ __forceinline__ ChunkGeom chunk_geom(int64_t c, const uint32_t* owner
 }
 
 __global__ void __launch_bounds__(kThreads)
-cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, FrameConst fc,
+cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
                  const uint32_t* __restrict__ owner, const uint32_t* __restrict__ chunk_offsets,
                  const uint32_t* __restrict__ n_chunks_dev, int64_t chunk_cap, uint32_t* __restrict__ masks,
                  unsigned long long* __restrict__ stats) {
+  const FrameConst fc = *fcp;
   const int64_t nch = min((int64_t)*n_chunks_dev, chunk_cap);
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
@@ -207,11 +208,12 @@ cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
       } else {
         const float4* r = reinterpret_cast<const float4*>(rec + q.g);
         const float4 t1 = __ldg(r + 0), t2 = __ldg(r + 1), t3 = __ldg(r + 2);
-        const float tau = inflate_tau(__uint_as_float(q.a.z));
+        const float tau_signed = __uint_as_float(q.a.z);
+        const float tau = inflate_tau(fabsf(tau_signed));
         const float xlo = (float)(tx * kTile), ylo = (float)(ty * kTile);
         const float xhi = xlo + kTile, yhi = ylo + kTile;
-        // depth key 0: the front of the ellipsoid reaches z_near
-        keep = q.a.w == 0u
+        // negative tau: the front of the ellipsoid reaches z_near
+        keep = tau_signed < 0.0f
                    ? frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, xlo, xhi, ylo, yhi, tau)
                    : frustum_hit<false>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, xlo, xhi, ylo, yhi, tau);
       }
@@ -226,10 +228,11 @@ cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
 }
 
 __global__ void __launch_bounds__(kThreads)
-cull_emit_kernel(const uint4* __restrict__ aux, FrameConst fc, const uint32_t* __restrict__ owner,
+cull_emit_kernel(const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp, const uint32_t* __restrict__ owner,
                  const uint32_t* __restrict__ chunk_offsets, const uint32_t* __restrict__ n_chunks_dev,
                  int64_t chunk_cap, const uint32_t* __restrict__ masks, const uint32_t* __restrict__ pair_offsets,
                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity) {
+  const FrameConst fc = *fcp;
   const int64_t nch = min((int64_t)*n_chunks_dev, chunk_cap);
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
@@ -293,7 +296,7 @@ aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st) {
   // 3. test
   const unsigned cblocks = (unsigned)std::max<int64_t>(
       std::min<int64_t>((ws->chunk_capacity + kWarps - 1) / kWarps, (int64_t)sm_count() * 16), 1);
-  cull_test_kernel<<<cblocks, kThreads, 0, st>>>(ws->records, ws->aux, ws->fc, ws->chunk_owner, ws->offsets,
+  cull_test_kernel<<<cblocks, kThreads, 0, st>>>(ws->records, ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets,
                                                  n_chunks, ws->chunk_capacity, ws->chunk_mask, ws->stats);
   e = check_launch("cull_test");
   if (e != AAAG_OK) return e;
@@ -302,7 +305,7 @@ aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st) {
                  ws->scan_partials, ws->stats, kStatPairs, n_pairs, st);
   if (e != AAAG_OK) return e;
   // 5. emit
-  cull_emit_kernel<<<cblocks, kThreads, 0, st>>>(ws->aux, ws->fc, ws->chunk_owner, ws->offsets, n_chunks,
+  cull_emit_kernel<<<cblocks, kThreads, 0, st>>>(ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets, n_chunks,
                                                  ws->chunk_capacity, ws->chunk_mask, ws->chunk_pair_offsets,
                                                  ws->keys[0], ws->vals[0], ws->capacity);
   return check_launch("cull_emit");

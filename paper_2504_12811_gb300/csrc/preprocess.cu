@@ -114,11 +114,12 @@ __device__ __forceinline__ bool tile_range(float p1, float p2, int size, int nti
 }
 
 __global__ void __launch_bounds__(256)
-preprocess_kernel(SceneDev s, FrameConst fc, Record* __restrict__ rec, uint4* __restrict__ aux,
+preprocess_kernel(SceneDev s, const FrameConst* __restrict__ fcp, Record* __restrict__ rec, uint4* __restrict__ aux,
                   uint32_t* __restrict__ chunks, unsigned long long* __restrict__ stats) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool visible = false;
   if (i < s.n) {
+    const FrameConst fc = *fcp;
     const float mx = s.means[3 * i + 0], my = s.means[3 * i + 1], mz = s.means[3 * i + 2];
     const float lx = s.log_scales[3 * i + 0], ly = s.log_scales[3 * i + 1],
                 lz = s.log_scales[3 * i + 2];
@@ -248,13 +249,32 @@ preprocess_kernel(SceneDev s, FrameConst fc, Record* __restrict__ rec, uint4* __
         out.t3 = t3;
         out.rgba = make_float4(fmaxf(cr, 0.0f), fmaxf(cg, 0.0f), fmaxf(cb, 0.0f), o_hat);
         rec[i] = out;
-        // depth key: quantised max(z_lo, znear), rounded down
-        const float zk = fmaxf(z_lo, fc.znear);
+        // Depth key: a lower bound of the depth t* of the maximum on every
+        // contributing ray.  In normalised Gaussian space the maximum u* of a
+        // ray from the camera c is the foot of the perpendicular from the
+        // origin, so u*.(u* - c) = 0: u* lies on the sphere |u|^2 = u.c, and
+        // contributing means |u*|^2 <= tau.  Hence u*.c_hat is in
+        // [0, tau/|c|] and the part of u* orthogonal to c_hat has length
+        // <= sqrt(tau); the view depth Z = A3.u + mu_z is then at least
+        //   mu_z - sqrt(tau) |A3_perp| + min(0, A3.c_hat) tau / |c|,
+        // with A3_perp the part of A3 orthogonal to c_hat.  This is never
+        // below the front of the tau-ellipsoid (|A3_perp| <= |A3|) and is much
+        // tighter for Gaussians seen head-on.  Quantised max(bound, znear),
+        // rounded down.
+        const float cn = sqrtf(ux * ux + uy * uy + uz * uz);
+        const float3 ch = (1.0f / cn) * f3(ux, uy, uz);
+        const float a3c = dot3(A3, ch);
+        const float3 A3p = A3 - a3c * ch;
+        float t_lo = vz - sqrtf(tau_c * dot3(A3p, A3p)) + fminf(a3c, 0.0f) * tau_c / cn;
+        t_lo -= 1e-5f * fabsf(t_lo) + 1e-6f;
+        const float zk = fmaxf(fmaxf(t_lo, z_lo), fc.znear);
         uint32_t dk = (__float_as_uint(zk) - fc.znear_bits) >> fc.depth_shift;
         const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
         dk = min(dk, dmax);
+        // tau_rho, negated when the front of the ellipsoid reaches znear (the
+        // tile test then truncates the frustum at the near plane)
         aux[i] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16),
-                            __float_as_uint(tau), dk);
+                            __float_as_uint(z_lo < fc.znear ? -tau : tau), dk);
         const uint32_t ntiles = (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1);
         chunks[i] = (ntiles + 31u) / 32u;
       }
@@ -274,7 +294,7 @@ aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_
   if (s.n == 0) return AAAG_OK;
   const int threads = 256;
   const int64_t blocks = (s.n + threads - 1) / threads;
-  preprocess_kernel<<<(unsigned)blocks, threads, 0, st>>>(s, ws->fc, ws->records, ws->aux, ws->counts,
+  preprocess_kernel<<<(unsigned)blocks, threads, 0, st>>>(s, ws->fc_dev, ws->records, ws->aux, ws->counts,
                                                           ws->stats);
   return check_launch("preprocess");
 }

@@ -15,6 +15,9 @@
 // the queue is full is an entry released early (counted as a potential
 // misorder).  Blending stops before the contributor that would take
 // transmittance below 1e-4.
+#include <algorithm>
+#include <cstring>
+
 #include <cuda_runtime.h>
 
 #include "aaag_internal.cuh"
@@ -44,14 +47,13 @@ struct ForwardBlend {
   }
 };
 
-__global__ void __launch_bounds__(kTilePixels, 3)
-render_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
-              const uint32_t* __restrict__ vals, const Record* __restrict__ rec, FrameConst fc,
-              float* __restrict__ rgb, float* __restrict__ alpha, float* __restrict__ final_T,
-              uint32_t* __restrict__ n_blended, unsigned long long* __restrict__ stats) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem& s = *reinterpret_cast<TileSmem*>(smem_raw);
-  const int tile = blockIdx.x;
+// Render one tile of one frame (all threads of the block).
+__device__ __forceinline__ void render_tile(TileSmem& s, int tile, const uint2* __restrict__ ranges,
+                                           const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                           const Record* __restrict__ rec, const FrameConst& fc,
+                                           float* __restrict__ rgb, float* __restrict__ alpha,
+                                           float* __restrict__ final_T, uint32_t* __restrict__ n_blended,
+                                           unsigned long long* __restrict__ stats) {
   const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
   const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
   const int px = tx * kTile + lx, py = ty * kTile + ly;
@@ -65,8 +67,8 @@ render_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ key
   bl.nblend = 0;
   unsigned long long neval = 0;
   uint32_t nmis = 0;
-  traverse_tile(s, ranges[tile], keys, vals, rec, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f,
-                        bl, neval, nmis);
+  traverse_tile(s, ranges[tile], keys, vals, rec, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f, bl, neval,
+                nmis);
 
   if (in_image) {
     const size_t HW = (size_t)fc.W * fc.H;
@@ -92,17 +94,117 @@ render_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ key
   }
 }
 
+__global__ void __launch_bounds__(kTilePixels, 3)
+render_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
+              const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
+              const FrameConst* __restrict__ fcp, float* __restrict__ rgb, float* __restrict__ alpha,
+              float* __restrict__ final_T, uint32_t* __restrict__ n_blended, unsigned long long* __restrict__ stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileSmem& s = *reinterpret_cast<TileSmem*>(smem_raw);
+  const FrameConst fc = *fcp;
+  render_tile(s, blockIdx.x, ranges, keys, vals, rec, fc, rgb, alpha, final_T, n_blended, stats);
+}
+
+// ---- K8: one persistent launch over the tiles of several frames.
+// Blocks take (frame, tile) work items in order from one atomic counter; the
+// frames' descriptors travel by value in the kernel parameters.  Nothing
+// waits on anything: every item is known at launch.
+struct RenderJob {
+  const uint2* ranges;
+  const uint32_t* keys;
+  const uint32_t* vals;
+  const Record* rec;
+  const FrameConst* fc;
+  float* rgb;
+  float* alpha;
+  float* final_T;
+  uint32_t* n_blended;
+  unsigned long long* stats;
+  uint32_t first;   // first work item of this frame
+  uint32_t tiles;
+};
+constexpr int kMaxBatch = 64;
+struct RenderBatch {
+  RenderJob job[kMaxBatch];
+  int n;
+  uint32_t total;
+};
+
+__global__ void __launch_bounds__(kTilePixels, 3)
+serve_render_kernel(const __grid_constant__ RenderBatch b, uint32_t* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileSmem& s = *reinterpret_cast<TileSmem*>(smem_raw);
+  __shared__ uint32_t s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    __syncthreads();
+    if (item >= b.total) break;
+    int j = 0;
+    while (j + 1 < b.n && b.job[j + 1].first <= item) ++j;
+    const RenderJob& J = b.job[j];
+    const FrameConst fc = *J.fc;
+    render_tile(s, (int)(item - J.first), J.ranges, J.keys, J.vals, J.rec, fc, J.rgb, J.alpha, J.final_T,
+                J.n_blended, J.stats);
+  }
+}
+
+int g_serve_blocks = 0;
+
 }  // namespace
 
-aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
-    configured = true;
+void prepare_render_kernels() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+  cudaFuncSetAttribute(serve_render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+  int dev = 0, sms = 1, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_render_kernel, kTilePixels, kTileSmemBytes);
+  g_serve_blocks = std::max(1, sms) * std::max(1, per_sm);
+  done = true;
+}
+
+aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, float* const* alpha, int n,
+                                cudaStream_t st) {
+  prepare_render_kernels();
+  RenderBatch b;
+  std::memset(&b, 0, sizeof(b));
+  uint32_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    const aaag_workspace* w = ws[i];
+    RenderJob& J = b.job[i];
+    const int alt = w->sorted_in_alt;
+    J.ranges = w->ranges;
+    J.keys = w->keys[alt];
+    J.vals = w->vals[alt];
+    J.rec = w->records;
+    J.fc = w->fc_dev;
+    J.rgb = rgb[i];
+    J.alpha = alpha[i];
+    J.final_T = w->final_T;
+    J.n_blended = w->n_blended;
+    J.stats = w->stats;
+    J.first = total;
+    J.tiles = (uint32_t)w->n_tiles;
+    total += J.tiles;
   }
+  b.n = n;
+  b.total = total;
+  uint32_t* counter = reinterpret_cast<uint32_t*>(ws[0]->stats + kStatBatchCounter);
+  if (cudaMemsetAsync(counter, 0, 4, st) != cudaSuccess) return check_launch("render_batch memset");
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g_serve_blocks, total));
+  serve_render_kernel<<<grid, kTilePixels, kTileSmemBytes, st>>>(b, counter);
+  return check_launch("serve_render");
+}
+
+aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st) {
+  prepare_render_kernels();
   const int alt = ws->sorted_in_alt;
   render_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kTileSmemBytes, st>>>(ws->ranges, ws->keys[alt], ws->vals[alt],
-                                                               ws->records, ws->fc, rgb, alpha, ws->final_T,
+                                                               ws->records, ws->fc_dev, rgb, alpha, ws->final_T,
                                                                ws->n_blended, ws->stats);
   return check_launch("render");
 }

@@ -228,6 +228,8 @@ void init_occupancy() {
 
 }  // namespace
 
+void prepare_sort_kernels() { init_occupancy(); }
+
 size_t radix_sort_scratch(int64_t n_max) {
   const int64_t tiles = (n_max + kSortTileKeys - 1) / kSortTileKeys;
   // hist [4][256] u32, counters [4] u32 (padded), lookback [tiles][256] u64, epoch u64, n u32

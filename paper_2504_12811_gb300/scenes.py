@@ -295,3 +295,60 @@ def poisson_arrivals(rate_hz: float, duration_s: float, seed: int = 2) -> np.nda
     n = int(rate_hz * duration_s * 1.5) + 16
     t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
     return t[t < duration_s]
+
+
+# ----------------------------------------------------------------------------
+# serving workload
+# ----------------------------------------------------------------------------
+
+SERVING_SCENES = {"s200k": 200_000, "s1m": 1_000_000, "s3m": 3_000_000}
+
+
+def serving_scenes(sizes=None, seed: int = 10):
+    """Resident scenes of the serving workload: uniform-cube Gaussians with SH
+    degree 3 (200k, 1M and 3M by default)."""
+    sizes = sizes or SERVING_SCENES
+    return {name: uniform_cube_scene(n, seed=seed + i, sh_degree=3)
+            for i, (name, n) in enumerate(sizes.items())}
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds from the start of the trace
+    scene: str
+    kind: str               # "vga" | "hd" | "stereo"
+    cams: list
+
+
+def request_cameras(kind: str, rng) -> list:
+    """Cameras of one request: a pose inside the scene (position uniform in
+    [-0.8, 0.8]^3, uniform look direction); stereo adds a second eye 64 mm
+    apart along the view x axis."""
+    pos = rng.uniform(-0.8, 0.8, 3)
+    d = rng.standard_normal(3)
+    d /= np.linalg.norm(d)
+    if kind == "vga":
+        return [make_camera(pos, forward=d, width=640, height=480, fov_x_deg=60.0)]
+    if kind == "hd":
+        return [make_camera(pos, forward=d, width=1920, height=1080, fov_x_deg=60.0)]
+    left = make_camera(pos, forward=d, width=1832, height=1920, fov_x_deg=110.0)
+    x_axis = left.viewmat[0, :3].astype(np.float64)
+    right_pos = pos + 0.064 * x_axis
+    return [make_camera(pos - 0.032 * x_axis, forward=d, width=1832, height=1920, fov_x_deg=110.0),
+            make_camera(right_pos - 0.032 * x_axis, forward=d, width=1832, height=1920, fov_x_deg=110.0)]
+
+
+def serving_trace(rate_hz: float = 400.0, duration_s: float = 5.0, seed: int = 2,
+                  scene_names=None, kinds=("vga", "hd", "stereo")) -> list:
+    """Poisson arrivals at `rate_hz`; each request picks a scene and a kind
+    uniformly (equal thirds) and a random pose."""
+    scene_names = list(scene_names or SERVING_SCENES)
+    t = poisson_arrivals(rate_hz, duration_s, seed)
+    rng = np.random.default_rng(seed + 1000)
+    out = []
+    for i, ti in enumerate(t):
+        kind = kinds[int(rng.integers(0, len(kinds)))]
+        scene = scene_names[int(rng.integers(0, len(scene_names)))]
+        out.append(Request(i, float(ti), scene, kind, request_cameras(kind, rng)))
+    return out

@@ -1,0 +1,210 @@
+"""Serving loop: resident scenes, admission by workspace memory, continuous
+batching of render requests into one persistent launch per batch.
+
+Every step that touches the GPU is a libaaag call (frame graphs and
+aaag_render_batch); this module only schedules.
+
+* Scenes stay resident in HBM (`DeviceScene`).
+* Slots: a memory budget is divided into workspaces that each fit the
+  largest view of the workload (any scene, any request resolution).  A request
+  (1 view, or 2 for stereo) is admitted when enough slots are free: admission
+  is by workspace memory.
+* Per slot and (scene, resolution), preprocess -> cull -> sort is a captured
+  CUDA graph re-aimed at each request's camera (aaag_graph_launch); slots run
+  on their own streams, so requests overlap on the device.
+* A batch of admitted views is rendered by one aaag_render_batch launch:
+  persistent blocks take (view, tile) items from a shared counter.
+* Continuous batching: while one batch renders, the next one is prepared on
+  other slots; a request arriving meanwhile joins the next batch as soon as
+  slots free up.  At most two batches are in flight.
+
+`plain_renderer` is the reference point: requests in arrival order, one at a
+time, each view rendered with aaag_render_frame on one stream.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import aaag
+
+
+@dataclass
+class Slot:
+    ws: "aaag.Workspace"
+    stream: torch.cuda.Stream
+    rgb_flat: torch.Tensor
+    alpha_flat: torch.Tensor
+    graphs: dict = field(default_factory=dict)
+
+    def outputs(self, cam):
+        hw = cam.width * cam.height
+        return (self.rgb_flat[: 3 * hw].view(3, cam.height, cam.width),
+                self.alpha_flat[:hw].view(cam.height, cam.width))
+
+
+class Server:
+    def __init__(self, scenes: dict, budget_bytes: int, max_width: int, max_height: int,
+                 pair_capacity: int, max_batch_views: int = 8, device="cuda", params=None):
+        self.scenes = {k: aaag.DeviceScene(v, device=device) for k, v in scenes.items()}
+        self.structs = {k: v.struct() for k, v in self.scenes.items()}
+        self.device = torch.device(device)
+        self.params = params if params is not None else aaag.make_params()
+        n_max = max(v.n for v in self.scenes.values())
+        ws_bytes = aaag.aaag_workspace_bytes(n_max, max_width, max_height, pair_capacity)
+        out_bytes = 16 * max_width * max_height
+        n_slots = max(2, int(budget_bytes // (ws_bytes + out_bytes)))
+        self.slot_bytes = ws_bytes + out_bytes
+        self.slots = []
+        for _ in range(n_slots):
+            ws = aaag.Workspace(n_max, max_width, max_height, pair_capacity, device=device)
+            self.slots.append(Slot(ws, torch.cuda.Stream(device=self.device),
+                                   torch.empty(3 * max_width * max_height, device=device),
+                                   torch.empty(max_width * max_height, device=device)))
+        self.render_stream = torch.cuda.Stream(device=self.device)
+        self.max_batch_views = max_batch_views
+
+    # -- graphs -----------------------------------------------------------
+    def _graph(self, slot: Slot, scene: str, cam):
+        key = (scene, cam.width, cam.height)
+        g = slot.graphs.get(key)
+        if g is None:
+            g = aaag.aaag_graph_create(self.structs[scene], aaag.make_camera(cam), self.params, slot.ws.handle,
+                                       aaag.AAAG_STAGE_PREPROCESS | aaag.AAAG_STAGE_CULL | aaag.AAAG_STAGE_SORT,
+                                       None, None, slot.stream.cuda_stream)
+            slot.graphs[key] = g
+        return g
+
+    def warm(self, requests):
+        """Capture every (slot, scene, resolution) graph the trace will need."""
+        shapes = {(r.scene, c.width, c.height): c for r in requests for c in r.cams}
+        for slot in self.slots:
+            for (scene, _, _), cam in shapes.items():
+                self._graph(slot, scene, cam)
+        torch.cuda.synchronize(self.device)
+
+    def close(self):
+        for slot in self.slots:
+            for g in slot.graphs.values():
+                aaag.aaag_graph_destroy(g)
+            slot.graphs.clear()
+
+    # -- one batch ----------------------------------------------------------
+    def _launch(self, views):
+        """views: list of (slot, request, camera).  Returns the done event."""
+        events = []
+        for slot, req, cam in views:
+            aaag.aaag_graph_launch(self._graph(slot, req.scene, cam), aaag.make_camera(cam),
+                                   slot.stream.cuda_stream)
+            ev = torch.cuda.Event()
+            ev.record(slot.stream)
+            events.append(ev)
+        for ev in events:
+            self.render_stream.wait_event(ev)
+        outs = [slot.outputs(cam) for slot, _, cam in views]
+        aaag.aaag_render_batch([slot.ws.handle for slot, _, _ in views], [o[0].data_ptr() for o in outs],
+                               [o[1].data_ptr() for o in outs], self.render_stream.cuda_stream)
+        done = torch.cuda.Event()
+        done.record(self.render_stream)
+        return done
+
+    def render_one(self, req):
+        """Render one request through the serving path and wait (for tests)."""
+        views = [(self.slots[i], req, cam) for i, cam in enumerate(req.cams)]
+        self._launch(views).synchronize()
+        return [slot.outputs(cam) for slot, _, cam in views]
+
+    # -- the loop -----------------------------------------------------------
+    def serve(self, requests, max_inflight: int = 2, capture=None):
+        """Replay `requests` in real time (arrival offsets from now).  Returns
+        per-request latency in seconds (completion observed by the host minus
+        arrival).  With a dict `capture`, the images of every request are
+        copied to it (rid -> [(rgb, alpha) per view], host tensors) before its
+        slots are reused; `self.max_views_in_flight` records the peak number
+        of views on the GPU."""
+        self.max_views_in_flight = 0
+        order = sorted(requests, key=lambda r: r.arrival)
+        pending = collections.deque()
+        free = list(self.slots)
+        inflight = []
+        lat = {}
+        i = 0
+        t0 = time.perf_counter()
+        while len(lat) < len(order):
+            now = time.perf_counter() - t0
+            while i < len(order) and order[i].arrival <= now:
+                pending.append(order[i])
+                i += 1
+            progressed = False
+            for b in list(inflight):
+                if b[0].query():
+                    tdone = time.perf_counter() - t0
+                    for r in b[1]:
+                        lat[r.rid] = tdone - r.arrival
+                    if capture is not None:
+                        for slot, r, cam in b[3]:
+                            rgb, alpha = slot.outputs(cam)
+                            capture.setdefault(r.rid, []).append((rgb.cpu(), alpha.cpu()))
+                    free.extend(b[2])
+                    inflight.remove(b)
+                    progressed = True
+            if pending and len(inflight) < max_inflight:
+                batch, views = [], []
+                while pending and len(free) >= len(pending[0].cams) and \
+                        len(views) + len(pending[0].cams) <= self.max_batch_views:
+                    r = pending.popleft()
+                    batch.append(r)
+                    for cam in r.cams:
+                        views.append((free.pop(), r, cam))
+                if batch:
+                    done = self._launch(views)
+                    inflight.append((done, batch, [v[0] for v in views], views))
+                    self.max_views_in_flight = max(self.max_views_in_flight,
+                                                   len(self.slots) - len(free))
+                    progressed = True
+            if not progressed:
+                time.sleep(20e-6)
+        return [lat[r.rid] for r in requests]
+
+
+def plain_renderer(scenes: dict, requests, max_width, max_height, pair_capacity, device="cuda", params=None):
+    """The per-frame renderer: requests in arrival order, one at a time, every
+    view through aaag_render_frame on one stream.  Returns per-request latency
+    (s) on the same clock as Server.serve."""
+    ds = {k: aaag.DeviceScene(v, device=device) for k, v in scenes.items()}
+    structs = {k: v.struct() for k, v in ds.items()}
+    n_max = max(v.n for v in ds.values())
+    ws = aaag.Workspace(n_max, max_width, max_height, pair_capacity, device=device)
+    stream = torch.cuda.Stream(device=device)
+    rgb = torch.empty(3 * max_width * max_height, device=device)
+    alpha = torch.empty(max_width * max_height, device=device)
+    prm = params if params is not None else aaag.make_params()
+    # warm-up: one frame per shape
+    for r in requests[:8]:
+        for cam in r.cams:
+            aaag.aaag_render_frame(structs[r.scene], aaag.make_camera(cam), prm, ws.handle, rgb.data_ptr(),
+                                   alpha.data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    lat = {}
+    order = sorted(requests, key=lambda r: r.arrival)
+    t0 = time.perf_counter()
+    for r in order:
+        while time.perf_counter() - t0 < r.arrival:
+            time.sleep(20e-6)
+        for cam in r.cams:
+            aaag.aaag_render_frame(structs[r.scene], aaag.make_camera(cam), prm, ws.handle, rgb.data_ptr(),
+                                   alpha.data_ptr(), stream.cuda_stream)
+        stream.synchronize()
+        lat[r.rid] = time.perf_counter() - t0 - r.arrival
+    return [lat[r.rid] for r in requests]
+
+
+def latency_summary(lat_s, duration_s, n_views):
+    a = np.asarray(lat_s) * 1e3
+    return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+            "mean_ms": float(a.mean()), "max_ms": float(a.max()), "requests": int(a.size),
+            "requests_per_s": a.size / duration_s, "views_per_s": n_views / duration_s}

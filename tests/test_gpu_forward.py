@@ -294,7 +294,7 @@ def test_host_argument_errors():
     ws = aaag.Workspace(scene.n, 128, 128, 1 << 16)
     st = aaag.current_stream()
     bad = aaag.make_camera(cams[0])
-    bad.width = 64
+    bad.width = 256          # larger than the workspace
     with pytest.raises(aaag.AaagError) as e:
         aaag.aaag_preprocess(ds.struct(), bad, aaag.make_params(), ws.handle, st)
     assert e.value.status == 1
