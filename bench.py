@@ -49,49 +49,59 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--capacity", type=int, default=48 << 20)
-    ap.add_argument("--serve-seconds", type=float, default=4.0,
-                    help="length of the Poisson serving trace (0 = skip serving)")
-    ap.add_argument("--serve-rate", type=float, default=400.0)
-    ap.add_argument("--serve-capacity", type=int, default=120 << 20)
-    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve", default="400:2,60:4",
+                    help="serving traces as rate_hz:seconds pairs ('' = skip serving)")
+    ap.add_argument("--serve-capacity", type=int, default=1 << 28)
+    ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     return ap.parse_args()
 
 
 def run_serving(args, dev):
     """Served-request latency: the continuous-batching server against the
     plain per-frame renderer, on the same Poisson trace of mixed requests over
-    three resident scenes."""
-    import numpy as np
+    three resident scenes, for each (rate, seconds) in --serve."""
     import torch
     from paper_2504_12811_gb300 import scenes, serve
     t = time.time()
     sc = scenes.serving_scenes()
-    trace = scenes.serving_trace(args.serve_rate, args.serve_seconds)
     gen_s = time.time() - t
-    n_views = sum(len(r.cams) for r in trace)
-    server = serve.Server(sc, int(args.serve_budget_gb * 2**30), 1920, 1920, args.serve_capacity,
-                          max_batch_views=8, device=dev)
-    n_slots = len(server.slots)
-    try:
-        server.warm(trace)
+    out = {"scenes": {k: v.n for k, v in sc.items()},
+           "mix": "equal thirds: 640x480 60deg, 1920x1080 60deg, stereo 2x1832x1920 110deg; "
+                  "poses uniform in [-0.8,0.8]^3 inside the scene, uniform look directions",
+           "latency": "host-observed completion (image in device memory) minus arrival",
+           "generation_s": gen_s, "runs": []}
+    for spec in [x for x in args.serve.split(",") if x]:
+        rate, seconds = (float(v) for v in spec.split(":"))
+        trace = scenes.serving_trace(rate, seconds, seed=2)
+        n_views = sum(len(r.cams) for r in trace)
+        server = serve.Server(sc, int(args.serve_budget_gb * 2**30), 1920, 1920, args.serve_capacity,
+                              max_batch_views=8, device=dev)
+        n_slots = len(server.slots)
+        try:
+            server.warm(trace)
+            t = time.time()
+            lat = server.serve_streams(trace)
+            ours_wall = time.time() - t
+            t = time.time()
+            lat_b = server.serve(trace)
+            batch_wall = time.time() - t
+        finally:
+            server.close()
+        del server
+        torch.cuda.empty_cache()
         t = time.time()
-        lat = server.serve(trace)
-        ours_wall = time.time() - t
-    finally:
-        server.close()
-    ours = serve.latency_summary(lat, max(ours_wall, args.serve_seconds), n_views)
-    del server
-    torch.cuda.empty_cache()
-    t = time.time()
-    lat_p = serve.plain_renderer(sc, trace, 1920, 1920, args.serve_capacity, device=dev)
-    plain_wall = time.time() - t
-    plain = serve.latency_summary(lat_p, max(plain_wall, args.serve_seconds), n_views)
-    return {"trace": {"rate_hz": args.serve_rate, "seconds": args.serve_seconds, "requests": len(trace),
-                      "views": n_views, "mix": "1/3 640x480 60deg, 1/3 1920x1080 60deg, 1/3 stereo 2x1832x1920 110deg",
-                      "scenes": {k: v.n for k, v in sc.items()}},
-            "server": dict(ours, slots=n_slots, budget_gb=args.serve_budget_gb, wall_s=ours_wall),
-            "plain_per_frame": dict(plain, wall_s=plain_wall),
-            "generation_s": gen_s}
+        lat_p = serve.plain_renderer(sc, trace, 1920, 1920, args.serve_capacity, device=dev)
+        plain_wall = time.time() - t
+        torch.cuda.empty_cache()
+        out["runs"].append({
+            "rate_hz": rate, "seconds": seconds, "requests": len(trace), "views": n_views,
+            "server": dict(serve.latency_summary(lat, max(ours_wall, seconds), n_views), slots=n_slots,
+                           budget_gb=args.serve_budget_gb, wall_s=ours_wall, mode="per-request pipelines"),
+            "server_batches": dict(serve.latency_summary(lat_b, max(batch_wall, seconds), n_views),
+                                   wall_s=batch_wall, mode="batch barrier, 8 views, 2 in flight"),
+            "plain_per_frame": dict(serve.latency_summary(lat_p, max(plain_wall, seconds), n_views),
+                                    wall_s=plain_wall)})
+    return out
 
 
 def dist_env():
@@ -407,7 +417,7 @@ def run_ours(args):
         "wall_s_timed": wall,
         "scene_generation_s": t_gen,
     }
-    if args.serve_seconds > 0:
+    if args.serve:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, cores, frame_s = cpu_baseline(scene, poses, args.cpu_seconds, W * H)

@@ -512,6 +512,7 @@ struct aaag_graph {
   aaag_params params;
   bool has_params;
   int sh_degree, width, height, stages;
+  int64_t n;
 };
 
 extern "C" {
@@ -586,6 +587,7 @@ aaag_status aaag_graph_create(const aaag_scene* scene, const aaag_camera* camera
   g->has_params = params != nullptr;
   if (params) g->params = *params;
   g->sh_degree = scene->sh_degree;
+  g->n = scene->n;
   g->width = camera->width;
   g->height = camera->height;
   g->stages = stages;
@@ -604,6 +606,7 @@ aaag_status aaag_graph_launch(aaag_graph* g, const aaag_camera* camera, cudaStre
   }
   aaag_workspace* ws = g->ws;
   // the workspace dimensions are those of the captured frame
+  ws->n = g->n;
   ws->width = g->width;
   ws->height = g->height;
   ws->tiles_x = tiles_of(g->width);

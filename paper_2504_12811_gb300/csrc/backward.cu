@@ -30,42 +30,64 @@
 namespace aaag {
 namespace {
 
+// Per-slot accumulators of the fast path, in shared memory after TileSmem:
+// [kMoments][kTilePixels]:  dL/dN0, dL/dNx, dL/dNy, dL/dD0, dL/dDx, dL/dDy
+// (3 each, tile-relative plane coefficients of render_core.cuh), dL/do_hat,
+// dL/dcolour (3).
+constexpr int kMoments = 22;
+constexpr size_t kBackwardSmemBytes = kTileSmemBytes + sizeof(float) * kMoments * kTilePixels;
+
 struct BackwardBlend {
   const Record* rec;
   float4* grad;        // [n][4] accumulators: dt1, dt2, dt3, (dr, dg, db, do_hat)
   const FrameConst* fc;
+  float* sacc;         // [kMoments][kTilePixels] shared
+  const uint32_t* vals;
+  float cxm, cym;      // principal point relative to the tile origin
   float T, Cr, Cg, Cb;
   bool done;
   uint32_t nblend;
   float X, Y;          // absolute pixel centre
+  float x, y;          // tile-relative pixel centre
   float gr, gg, gb;    // dL/dRGB
   float ga;            // dL/dalpha (output alpha)
   float Fr, Fg, Fb;    // forward output colour (includes T_final bg)
   float Tfinal;
+  float acc[kMoments];
+  bool has;
 
-  __device__ __forceinline__ void blend(float a, uint32_t gid) {
+  // compositing part shared by both paths: returns dL/dalpha (0 when done)
+  __device__ __forceinline__ bool composite(float a, float4 c, float& dal, float& w) {
     const float Tn = T * (1.0f - a);
     if (Tn < kTStop) {
       done = true;
-      return;
+      return false;
     }
-    const float4* r = reinterpret_cast<const float4*>(rec + gid);
-    const float4 c = __ldg(r + 3);
-    const float w = a * T;
+    w = a * T;
     Cr = fmaf(c.x, w, Cr);
     Cg = fmaf(c.y, w, Cg);
     Cb = fmaf(c.z, w, Cb);
     const float inv1ma = 1.0f / (1.0f - a);
-    // dL/dalpha from the colour and the output alpha
-    const float dal = gr * (c.x * T - (Fr - Cr) * inv1ma) + gg * (c.y * T - (Fg - Cg) * inv1ma) +
-                      gb * (c.z * T - (Fb - Cb) * inv1ma) + ga * Tfinal * inv1ma;
-    // alpha = min(0.99, o_hat exp(-rho^2/2)): recompute rho^2 at this pixel
+    dal = gr * (c.x * T - (Fr - Cr) * inv1ma) + gg * (c.y * T - (Fg - Cg) * inv1ma) +
+          gb * (c.z * T - (Fb - Cb) * inv1ma) + ga * Tfinal * inv1ma;
+    T = Tn;
+    ++nblend;
+    return true;
+  }
+
+  // queued contributor: its planes are recomputed at this pixel and the
+  // gradient goes straight to the Gaussian's accumulator
+  __device__ __forceinline__ void blend(float a, uint32_t gid) {
+    const float4* r = reinterpret_cast<const float4*>(rec + gid);
+    const float4 c = __ldg(r + 3);
+    float dal, w;
+    if (!composite(a, c, dal, w)) return;
     const float4 t1 = __ldg(r + 0), t2 = __ldg(r + 1), t3 = __ldg(r + 2);
-    const float cxm = fc->cx - X, cym = fc->cy - Y;
-    const float3 n1 = f3(fmaf(cxm, t3.x, fc->fx * t1.x), fmaf(cxm, t3.y, fc->fx * t1.y), fmaf(cxm, t3.z, fc->fx * t1.z));
-    const float h1 = fmaf(cxm, t3.w, fc->fx * t1.w);
-    const float3 n2 = f3(fmaf(cym, t3.x, fc->fy * t2.x), fmaf(cym, t3.y, fc->fy * t2.y), fmaf(cym, t3.z, fc->fy * t2.z));
-    const float h2 = fmaf(cym, t3.w, fc->fy * t2.w);
+    const float cx_ = fc->cx - X, cy_ = fc->cy - Y;
+    const float3 n1 = f3(fmaf(cx_, t3.x, fc->fx * t1.x), fmaf(cx_, t3.y, fc->fx * t1.y), fmaf(cx_, t3.z, fc->fx * t1.z));
+    const float h1 = fmaf(cx_, t3.w, fc->fx * t1.w);
+    const float3 n2 = f3(fmaf(cy_, t3.x, fc->fy * t2.x), fmaf(cy_, t3.y, fc->fy * t2.y), fmaf(cy_, t3.z, fc->fy * t2.z));
+    const float h2 = fmaf(cy_, t3.w, fc->fy * t2.w);
     const float3 num = h1 * n2 - h2 * n1;
     const float3 dv = cross3(n1, n2);
     const float inv = 1.0f / dot3(dv, dv);
@@ -84,28 +106,129 @@ struct BackwardBlend {
       const float3 dn2 = h1 * dnum + cross3(ddv, n1);
       g1 = make_float4(fc->fx * dn1.x, fc->fx * dn1.y, fc->fx * dn1.z, fc->fx * dh1);
       g2 = make_float4(fc->fy * dn2.x, fc->fy * dn2.y, fc->fy * dn2.z, fc->fy * dh2);
-      g3 = make_float4(cxm * dn1.x + cym * dn2.x, cxm * dn1.y + cym * dn2.y, cxm * dn1.z + cym * dn2.z,
-                       cxm * dh1 + cym * dh2);
+      g3 = make_float4(cx_ * dn1.x + cy_ * dn2.x, cx_ * dn1.y + cy_ * dn2.y, cx_ * dn1.z + cy_ * dn2.z,
+                       cx_ * dh1 + cy_ * dh2);
     }
-    float4* acc = grad + 4 * (size_t)gid;
-    atomicAdd(acc + 0, g1);
-    atomicAdd(acc + 1, g2);
-    atomicAdd(acc + 2, g3);
-    atomicAdd(acc + 3, make_float4(gr * w, gg * w, gb * w, doh));
-    T = Tn;
-    ++nblend;
+    float4* acc4 = grad + 4 * (size_t)gid;
+    atomicAdd(acc4 + 0, g1);
+    atomicAdd(acc4 + 1, g2);
+    atomicAdd(acc4 + 2, g3);
+    atomicAdd(acc4 + 3, make_float4(gr * w, gg * w, gb * w, doh));
+  }
+
+  // the staged Gaussian k: gradient moments stay in registers until the
+  // warp-level reduction at the end of item k
+  __device__ __forceinline__ void blend_new(float a, uint32_t gid, const EvalState& ev) {
+    const float4 c = __ldg(reinterpret_cast<const float4*>(rec + gid) + 3);
+    float dal, w;
+    if (!composite(a, c, dal, w)) return;
+    const float G = __expf(-0.5f * ev.rho2);
+    const float raw = c.w * G;
+    if (raw < kAlphaMax) {
+      const float drho2 = -0.5f * dal * raw;
+      const float sn = 2.0f * drho2 * ev.inv;
+      const float sd = -2.0f * drho2 * ev.rho2 * ev.inv;
+      const float dn[3] = {sn * ev.n0, sn * ev.n1, sn * ev.n2};
+      const float ddv[3] = {sd * ev.d0, sd * ev.d1, sd * ev.d2};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        acc[i] = dn[i];
+        acc[3 + i] = x * dn[i];
+        acc[6 + i] = y * dn[i];
+        acc[9 + i] = ddv[i];
+        acc[12 + i] = x * ddv[i];
+        acc[15 + i] = y * ddv[i];
+      }
+      acc[18] = dal * G;
+    }
+    acc[19] = gr * w;
+    acc[20] = gg * w;
+    acc[21] = gb * w;
+    has = true;
+  }
+
+  __device__ __forceinline__ void end_item(int k) {
+    const unsigned any = __ballot_sync(0xffffffffu, has);
+    if (!any) return;
+    if (!has) {
+#pragma unroll
+      for (int i = 0; i < kMoments; ++i) acc[i] = 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < kMoments; ++i) {
+      float v = acc[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      acc[i] = v;
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+      for (int i = 0; i < kMoments; ++i)
+        if (acc[i] != 0.0f) atomicAdd(&sacc[i * kTilePixels + k], acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < kMoments; ++i) acc[i] = 0.0f;
+    has = false;
+  }
+
+  // block-converged: convert each staged Gaussian's moments to gradients of
+  // its T_view rows, one set of vector atomics per (tile, Gaussian)
+  __device__ __forceinline__ void end_batch(uint32_t b0, int cnt) {
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < cnt) {
+      float m[kMoments];
+      bool nz = false;
+#pragma unroll
+      for (int i = 0; i < kMoments; ++i) {
+        m[i] = sacc[i * kTilePixels + t];
+        nz |= m[i] != 0.0f;
+        sacc[i * kTilePixels + t] = 0.0f;
+      }
+      if (nz) {
+        const uint32_t gid = vals[b0 + t];
+        const float4* r = reinterpret_cast<const float4*>(rec + gid);
+        const float4 t1 = __ldg(r + 0), t2 = __ldg(r + 1), t3 = __ldg(r + 2);
+        const float3 T3 = f3(t3.x, t3.y, t3.z);
+        const float3 Uv = f3(fmaf(cxm, t3.x, fc->fx * t1.x), fmaf(cxm, t3.y, fc->fx * t1.y), fmaf(cxm, t3.z, fc->fx * t1.z));
+        const float Uw = fmaf(cxm, t3.w, fc->fx * t1.w);
+        const float3 Wv = f3(fmaf(cym, t3.x, fc->fy * t2.x), fmaf(cym, t3.y, fc->fy * t2.y), fmaf(cym, t3.z, fc->fy * t2.z));
+        const float Ww = fmaf(cym, t3.w, fc->fy * t2.w);
+        const float3 gN0 = f3(m[0], m[1], m[2]), gNx = f3(m[3], m[4], m[5]), gNy = f3(m[6], m[7], m[8]);
+        const float3 gD0 = f3(m[9], m[10], m[11]), gDx = f3(m[12], m[13], m[14]), gDy = f3(m[15], m[16], m[17]);
+        // N0 = Uw Wv - Ww Uv, Nx = Ww T3 - T3w Wv, Ny = T3w Uv - Uw T3,
+        // D0 = Uv x Wv, Dx = Wv x T3, Dy = T3 x Uv
+        const float gUw = dot3(gN0, Wv) - dot3(gNy, T3);
+        const float gWw = -dot3(gN0, Uv) + dot3(gNx, T3);
+        const float gTw = -dot3(gNx, Wv) + dot3(gNy, Uv);
+        const float3 gUv = (-Ww) * gN0 + t3.w * gNy + cross3(Wv, gD0) + cross3(gDy, T3);
+        const float3 gWv = Uw * gN0 - t3.w * gNx + cross3(gD0, Uv) + cross3(T3, gDx);
+        const float3 gTv = Ww * gNx - Uw * gNy + cross3(gDx, Wv) + cross3(Uv, gDy);
+        // U = fx t1 + cxm t3, W = fy t2 + cym t3
+        const float4 g1 = make_float4(fc->fx * gUv.x, fc->fx * gUv.y, fc->fx * gUv.z, fc->fx * gUw);
+        const float4 g2 = make_float4(fc->fy * gWv.x, fc->fy * gWv.y, fc->fy * gWv.z, fc->fy * gWw);
+        const float4 g3 = make_float4(cxm * gUv.x + cym * gWv.x + gTv.x, cxm * gUv.y + cym * gWv.y + gTv.y,
+                                      cxm * gUv.z + cym * gWv.z + gTv.z, cxm * gUw + cym * gWw + gTw);
+        float4* acc4 = grad + 4 * (size_t)gid;
+        atomicAdd(acc4 + 0, g1);
+        atomicAdd(acc4 + 1, g2);
+        atomicAdd(acc4 + 2, g3);
+        atomicAdd(acc4 + 3, make_float4(m[19], m[20], m[21], m[18]));
+      }
+    }
   }
 };
 
 __global__ void __launch_bounds__(kTilePixels, 2)
 render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
                        const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
-                       const FrameConst* __restrict__ fcp, const float* __restrict__ rgb, const float* __restrict__ drgb,
-                       const float* __restrict__ dalpha, const float* __restrict__ final_T,
-                       const uint32_t* __restrict__ n_blended, float4* __restrict__ grad,
-                       unsigned long long* __restrict__ stats) {
+                       const FrameConst* __restrict__ fcp, const float* __restrict__ rgb,
+                       const float* __restrict__ drgb, const float* __restrict__ dalpha,
+                       const float* __restrict__ final_T, const uint32_t* __restrict__ n_blended,
+                       float4* __restrict__ grad, unsigned long long* __restrict__ stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileSmem& s = *reinterpret_cast<TileSmem*>(smem_raw);
+  float* sacc = reinterpret_cast<float*>(smem_raw + kTileSmemBytes);
   const FrameConst fc = *fcp;
   const int tile = blockIdx.x;
   const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
@@ -114,16 +237,26 @@ render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restr
   const bool in_image = px < fc.W && py < fc.H;
   const size_t HW = (size_t)fc.W * fc.H;
   const size_t p = in_image ? (size_t)py * fc.W + px : 0;
+  for (int i = threadIdx.x; i < kMoments * kTilePixels; i += kTilePixels) sacc[i] = 0.0f;
 
   BackwardBlend bl;
   bl.rec = rec;
   bl.grad = grad;
   bl.fc = &fc;
+  bl.sacc = sacc;
+  bl.vals = vals;
+  bl.cxm = fc.cx - (float)(tx * kTile);
+  bl.cym = fc.cy - (float)(ty * kTile);
   bl.T = 1.0f;
   bl.Cr = bl.Cg = bl.Cb = 0.0f;
   bl.nblend = 0;
   bl.X = (float)px + 0.5f;
   bl.Y = (float)py + 0.5f;
+  bl.x = (float)lx + 0.5f;
+  bl.y = (float)ly + 0.5f;
+#pragma unroll
+  for (int i = 0; i < kMoments; ++i) bl.acc[i] = 0.0f;
+  bl.has = false;
   float Tf = 1.0f;
   if (in_image) {
     bl.gr = drgb[p];
@@ -138,13 +271,11 @@ render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restr
     bl.gr = bl.gg = bl.gb = bl.ga = bl.Fr = bl.Fg = bl.Fb = 0.0f;
   }
   bl.Tfinal = Tf;
-  // a pixel with no incoming gradient still replays (the block walks in
-  // lockstep) but skips its blends
   bl.done = !in_image;
   unsigned long long neval = 0;
   uint32_t nmis = 0;
-  traverse_tile(s, ranges[tile], keys, vals, rec, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f, bl,
-                        neval, nmis);
+  __syncthreads();
+  traverse_tile<true>(s, ranges[tile], keys, vals, rec, fc, tx, ty, bl.x, bl.y, bl, neval, nmis);
   // the replay must reproduce the forward blend count
   const bool mismatch = in_image && bl.nblend != n_blended[p];
   const unsigned ball = __ballot_sync(0xffffffffu, mismatch);
@@ -368,7 +499,8 @@ preprocess_backward_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const
 void prepare_backward_kernels() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(render_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+  cudaFuncSetAttribute(render_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kBackwardSmemBytes);
   done = true;
 }
 
@@ -378,7 +510,7 @@ aaag_status launch_render_backward(const SceneDev& s, aaag_workspace* ws, const 
     return check_launch("backward memset");
   prepare_backward_kernels();
   const int alt = ws->sorted_in_alt;
-  render_backward_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kTileSmemBytes, st>>>(
+  render_backward_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kBackwardSmemBytes, st>>>(
       ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->fc_dev, rgb, drgb, dalpha, ws->final_T,
       ws->n_blended, ws->grad_acc, ws->stats);
   aaag_status e = check_launch("render_backward");

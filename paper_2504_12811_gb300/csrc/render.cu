@@ -45,6 +45,7 @@ struct ForwardBlend {
     T = Tn;
     ++nblend;
   }
+  __device__ __forceinline__ void blend_new(float a, uint32_t gid, const EvalState&) { blend(a, gid); }
 };
 
 // Render one tile of one frame (all threads of the block).
@@ -67,8 +68,8 @@ __device__ __forceinline__ void render_tile(TileSmem& s, int tile, const uint2* 
   bl.nblend = 0;
   unsigned long long neval = 0;
   uint32_t nmis = 0;
-  traverse_tile(s, ranges[tile], keys, vals, rec, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f, bl, neval,
-                nmis);
+  traverse_tile<false>(s, ranges[tile], keys, vals, rec, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f, bl,
+                       neval, nmis);
 
   if (in_image) {
     const size_t HW = (size_t)fc.W * fc.H;

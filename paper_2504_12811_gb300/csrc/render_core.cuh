@@ -39,7 +39,7 @@ constexpr int kQueue = 16;   // per-pixel re-sort queue entries (power of two)
 struct TileSmem {
   float4 a[kTilePixels];  // N0.xyz, o_hat
   float4 b[kTilePixels];  // Nx.xyz, L_next: lower bound of t* for every later pair
-  float4 c[kTilePixels];  // Ny.xyz, Gaussian index (bits)
+  float4 c[kTilePixels];  // Ny.xyz, tau+: |num|^2 > tau+ |d|^2 rules out alpha >= 1/255
   float4 d[kTilePixels];  // D0.xyz, G.x
   float4 e[kTilePixels];  // Dx.xyz, G.y
   float4 f[kTilePixels];  // Dy.xyz, G.z
@@ -82,7 +82,10 @@ __device__ __forceinline__ void stage_one(TileSmem& s, int slot, const Record* r
   const float3 G = fxfy * fma3(t1.w, crs(A2, T3), fma3(t2.w, crs(T3, A1), t3.w * crs(A1, A2)));
   s.a[slot] = make_float4(N0.x, N0.y, N0.z, cw.w);
   s.b[slot] = make_float4(Nx.x, Nx.y, Nx.z, Lnext);
-  s.c[slot] = make_float4(Ny.x, Ny.y, Ny.z, __uint_as_float(gid));
+  // rho^2 <= tau_rho exactly where o_hat exp(-rho^2/2) >= 1/255; the margin
+  // keeps the division-free prefilter conservative under float32 rounding
+  const float tau = 2.0f * logf(cw.w * 255.0f);
+  s.c[slot] = make_float4(Ny.x, Ny.y, Ny.z, fmaf(tau, 1e-4f, tau) + 1e-4f);
   s.d[slot] = make_float4(D0.x, D0.y, D0.z, G.x);
   s.e[slot] = make_float4(Dx.x, Dx.y, Dx.z, G.y);
   s.f[slot] = make_float4(Dy.x, Dy.y, Dy.z, G.z);
@@ -121,10 +124,24 @@ struct SmemQueue {
   }
 };
 
+// Values of the current evaluation handed to a blend of the newly evaluated
+// (staged) Gaussian: its slot and the pixel's num, d, 1/|d|^2 and rho^2.
+struct EvalState {
+  int k;
+  float n0, n1, n2, d0, d1, d2, inv, rho2;
+};
+
 // Traverse one tile for one pixel.  Blender must provide:
-//   bool done;                                  pixel finished
-//   void blend(float alpha, uint32_t gid);      blend one contributor (may set done)
-template <class Blender>
+//   bool done;                                       pixel finished
+//   void blend(float alpha, uint32_t gid);           blend a queued contributor
+//   void blend_new(float alpha, uint32_t gid, const EvalState&);
+//                                                    blend the staged Gaussian k
+// With CONVERGENT, every lane runs every iteration (no early exit from the
+// pair loop) and the Blender also provides
+//   void end_item(int k);                            warp-converged, after item k
+//   void end_batch(uint32_t b0, int cnt);            block-converged, after a batch
+// The arithmetic, and so every blend decision, is the same either way.
+template <bool CONVERGENT, class Blender>
 __device__ __forceinline__ void traverse_tile(TileSmem& s, const uint2 range, const uint32_t* __restrict__ keys,
                                               const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
                                               const FrameConst& fc, int tile_x, int tile_y, float x, float y,
@@ -145,62 +162,73 @@ __device__ __forceinline__ void traverse_tile(TileSmem& s, const uint2 range, co
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kTilePixels, range.y - b0);
-    if (!bl.done) {
-      neval += (unsigned long long)cnt;
+    if (CONVERGENT || !bl.done) {
+      if (!bl.done) neval += (unsigned long long)cnt;
       for (int k = 0; k < cnt; ++k) {
-        const float4 a = s.a[k], bq = s.b[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
-        const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
-        const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
-        const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
-        const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
-        const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
-        const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
-        const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
-        const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
-        const float inv = __fdividef(1.0f, dd);
-        const float rho2 = nn * inv;
-        const float raw = a.w * __expf(-0.5f * rho2);
-        if (raw >= kAlphaMin) {
-          const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
-          if (ts >= fc.znear) {
-            const float Lnext = bq.w;
-            const float ca = fminf(raw, kAlphaMax);
-            const uint32_t cg = __float_as_uint(c.w);
-            // 1. queued entries in front of the new one that nothing later can precede
-            while (q.n > 0 && !bl.done) {
-              const float ft = q.front_t();
-              if (!(ft <= ts && ft < Lnext)) break;
-              bl.blend(q.front_a(), q.front_g());
-              q.pop();
-            }
-            if (bl.done) break;
-            if (ts < Lnext) {
-              // 2. the new contributor, then the rest below L_next
-              bl.blend(ca, cg);
-              while (q.n > 0 && !bl.done && q.front_t() < Lnext) {
+        if (!bl.done) {
+          const float4 a = s.a[k], bq = s.b[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
+          const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
+          const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
+          const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
+          const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
+          const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
+          const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
+          const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
+          const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+          // rho^2 > tau+ rules out alpha >= 1/255 without a division
+          if (nn <= c.w * dd) {
+            const float inv = __fdividef(1.0f, dd);
+            const float rho2 = nn * inv;
+            const float raw = a.w * __expf(-0.5f * rho2);
+            const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
+            if (raw >= kAlphaMin && ts >= fc.znear) {
+              const float Lnext = bq.w;
+              const float ca = fminf(raw, kAlphaMax);
+              const uint32_t cg = vals[b0 + k];
+              const EvalState ev{k, n0, n1, n2, d0, d1, d2, inv, rho2};
+              // 1. queued entries in front of the new one that nothing later can precede
+              while (q.n > 0 && !bl.done) {
+                const float ft = q.front_t();
+                if (!(ft <= ts && ft < Lnext)) break;
                 bl.blend(q.front_a(), q.front_g());
                 q.pop();
               }
-              if (bl.done) break;
-            } else {
-              // 3. queue it
-              if (q.n == kQueue) {
-                ++nmis;
-                if (ts < q.front_t()) {
-                  bl.blend(ca, cg);
-                  if (bl.done) break;
-                  continue;
+              if (!bl.done) {
+                if (ts < Lnext) {
+                  // 2. the new contributor, then the rest below L_next
+                  bl.blend_new(ca, cg, ev);
+                  while (q.n > 0 && !bl.done && q.front_t() < Lnext) {
+                    bl.blend(q.front_a(), q.front_g());
+                    q.pop();
+                  }
+                } else {
+                  // 3. queue it; when full, release the nearer of the front and
+                  // the new entry early (a potential misorder)
+                  bool insert = true;
+                  if (q.n == kQueue) {
+                    ++nmis;
+                    if (ts < q.front_t()) {
+                      bl.blend_new(ca, cg, ev);
+                      insert = false;
+                    } else {
+                      bl.blend(q.front_a(), q.front_g());
+                      q.pop();
+                    }
+                  }
+                  if (insert && !bl.done) q.insert(ts, ca, cg);
                 }
-                bl.blend(q.front_a(), q.front_g());
-                q.pop();
-                if (bl.done) break;
               }
-              q.insert(ts, ca, cg);
             }
           }
         }
+        if constexpr (CONVERGENT) {
+          bl.end_item(k);
+        } else {
+          if (bl.done) break;
+        }
       }
     }
+    if constexpr (CONVERGENT) bl.end_batch(b0, cnt);
     __syncthreads();
   }
   while (q.n > 0 && !bl.done) {

@@ -14,9 +14,13 @@ aaag_render_batch); this module only schedules.
   on their own streams, so requests overlap on the device.
 * A batch of admitted views is rendered by one aaag_render_batch launch:
   persistent blocks take (view, tile) items from a shared counter.
-* Continuous batching: while one batch renders, the next one is prepared on
-  other slots; a request arriving meanwhile joins the next batch as soon as
-  slots free up.  At most two batches are in flight.
+* Continuous batching (`serve`): while one batch renders, the next one is
+  prepared on other slots; a request arriving meanwhile joins the next batch
+  as soon as slots free up.  At most two batches are in flight.
+* Per-request pipelines (`serve_streams`): requests are admitted in arrival
+  order as slots free up and run concurrently without a batch barrier; the
+  views of a request (two for stereo) share one persistent render launch and
+  the request completes on its own event.
 
 `plain_renderer` is the reference point: requests in arrival order, one at a
 time, each view rendered with aaag_render_frame on one stream.
@@ -111,6 +115,65 @@ class Server:
         done = torch.cuda.Event()
         done.record(self.render_stream)
         return done
+
+    def _launch_request(self, req, slots):
+        """Per-request pipeline: every view's frame graph on its own slot
+        stream, then one persistent render over the request's views on the
+        first slot's stream.  Returns the completion event."""
+        for slot, cam in zip(slots, req.cams):
+            aaag.aaag_graph_launch(self._graph(slot, req.scene, cam), aaag.make_camera(cam),
+                                   slot.stream.cuda_stream)
+        lead = slots[0].stream
+        for slot in slots[1:]:
+            ev = torch.cuda.Event()
+            ev.record(slot.stream)
+            lead.wait_event(ev)
+        outs = [slot.outputs(cam) for slot, cam in zip(slots, req.cams)]
+        aaag.aaag_render_batch([slot.ws.handle for slot in slots], [o[0].data_ptr() for o in outs],
+                               [o[1].data_ptr() for o in outs], lead.cuda_stream)
+        done = torch.cuda.Event()
+        done.record(lead)
+        return done
+
+    def serve_streams(self, requests, capture=None):
+        """Continuous per-request pipelines: requests are admitted in arrival
+        order as soon as their views fit into free slots (workspace memory),
+        run concurrently on their slots' streams, and complete individually.
+        Same return value and `capture` as `serve`."""
+        self.max_views_in_flight = 0
+        order = sorted(requests, key=lambda r: r.arrival)
+        pending = collections.deque()
+        free = list(self.slots)
+        inflight = []
+        lat = {}
+        i = 0
+        t0 = time.perf_counter()
+        while len(lat) < len(order):
+            now = time.perf_counter() - t0
+            while i < len(order) and order[i].arrival <= now:
+                pending.append(order[i])
+                i += 1
+            progressed = False
+            for item in list(inflight):
+                done, req, slots = item
+                if done.query():
+                    lat[req.rid] = time.perf_counter() - t0 - req.arrival
+                    if capture is not None:
+                        for slot, cam in zip(slots, req.cams):
+                            rgb, alpha = slot.outputs(cam)
+                            capture.setdefault(req.rid, []).append((rgb.cpu(), alpha.cpu()))
+                    free.extend(slots)
+                    inflight.remove(item)
+                    progressed = True
+            while pending and len(free) >= len(pending[0].cams):
+                req = pending.popleft()
+                slots = [free.pop() for _ in req.cams]
+                inflight.append((self._launch_request(req, slots), req, slots))
+                self.max_views_in_flight = max(self.max_views_in_flight, len(self.slots) - len(free))
+                progressed = True
+            if not progressed:
+                time.sleep(20e-6)
+        return [lat[r.rid] for r in requests]
 
     def render_one(self, req):
         """Render one request through the serving path and wait (for tests)."""

@@ -100,17 +100,20 @@ def test_serving_results_same_alone_and_in_mix():
     serve, server, sc, reqs = small_serving_setup()
     try:
         server.warm(reqs)
-        captured = {}
+        captured, captured_s = {}, {}
         lat = server.serve(reqs, capture=captured)
+        assert len(lat) == len(reqs) and all(x > 0 for x in lat)
+        lat = server.serve_streams(reqs, capture=captured_s)
         assert len(lat) == len(reqs) and all(x > 0 for x in lat)
         ds = {k: aaag.DeviceScene(v) for k, v in sc.items()}
         ws = aaag.Workspace(60_000, 320, 272, 1 << 21)
         worst = 0.0
         for r in reqs:
-            for (rgb_mix, a_mix), cam in zip(captured[r.rid], r.cams):
-                rgb_alone, a_alone = single_frame(ds[r.scene].struct(), cam, ws)
-                worst = max(worst, float((rgb_mix - rgb_alone).abs().max()),
-                            float((a_mix - a_alone).abs().max()))
+            for cap in (captured, captured_s):
+                for (rgb_mix, a_mix), cam in zip(cap[r.rid], r.cams):
+                    rgb_alone, a_alone = single_frame(ds[r.scene].struct(), cam, ws)
+                    worst = max(worst, float((rgb_mix - rgb_alone).abs().max()),
+                                float((a_mix - a_alone).abs().max()))
         # the same kernels on the same inputs: identical in practice, and
         # within the image tolerance in any case
         assert worst <= 2e-3
@@ -124,8 +127,9 @@ def test_admission_respects_memory_budget():
     try:
         assert len(server.slots) == 2
         server.warm(reqs)
-        lat = server.serve(reqs)
-        assert len(lat) == len(reqs)
-        assert server.max_views_in_flight <= len(server.slots)
+        for run in (server.serve, server.serve_streams):
+            lat = run(reqs)
+            assert len(lat) == len(reqs)
+            assert server.max_views_in_flight <= len(server.slots)
     finally:
         server.close()
