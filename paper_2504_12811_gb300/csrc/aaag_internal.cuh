@@ -25,6 +25,7 @@ struct FrameConst {
   float tv[3];          // world -> view translation
   float o[3];           // camera origin in world space: -Rv^-1 tv
   float fx, fy, cx, cy;
+  float side[4][3];     // inward unit normals of the image frustum's side planes (view space)
   int W, H, tiles_x, tiles_y;
   float znear;
   float bg[3];

@@ -129,6 +129,18 @@ aaag_status make_frame(const aaag_camera* cam, const aaag_params* prm, int sh_de
   fc->cy = cam->cy;
   fc->W = cam->width;
   fc->H = cam->height;
+  {
+    // pixel x >= 0, x <= W, y >= 0, y <= H as half-spaces through the camera
+    const double W = cam->width, H = cam->height;
+    const double n[4][3] = {{cam->fx, 0.0, cam->cx},
+                            {-cam->fx, 0.0, W - cam->cx},
+                            {0.0, cam->fy, cam->cy},
+                            {0.0, -cam->fy, H - cam->cy}};
+    for (int j = 0; j < 4; ++j) {
+      const double len = std::sqrt(n[j][0] * n[j][0] + n[j][1] * n[j][1] + n[j][2] * n[j][2]);
+      for (int c = 0; c < 3; ++c) fc->side[j][c] = (float)(n[j][c] / len);
+    }
+  }
   fc->tiles_x = ws->tiles_x;
   fc->tiles_y = ws->tiles_y;
   fc->znear = cam->znear;

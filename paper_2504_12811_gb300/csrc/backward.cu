@@ -35,9 +35,12 @@ namespace {
 // (3 each, tile-relative plane coefficients of render_core.cuh), dL/do_hat,
 // dL/dcolour (3).
 constexpr int kMoments = 22;
-constexpr size_t kBackwardSmemBytes = kTileSmemBytes + sizeof(float) * kMoments * kTilePixels;
+constexpr size_t kStageBytes = sizeof(TileSmem<IndexQueue>);
+constexpr size_t kBackwardSmemBytes = kStageBytes + sizeof(float) * kMoments * kTilePixels;
 
 struct BackwardBlend {
+  using Queue = IndexQueue;
+  const StageSmem* st;
   const Record* rec;
   float4* grad;        // [n][4] accumulators: dt1, dt2, dt3, (dr, dg, db, do_hat)
   const FrameConst* fc;
@@ -118,12 +121,13 @@ struct BackwardBlend {
 
   // the staged Gaussian k: gradient moments stay in registers until the
   // warp-level reduction at the end of item k
-  __device__ __forceinline__ void blend_new(float a, uint32_t gid, const EvalState& ev) {
-    const float4 c = __ldg(reinterpret_cast<const float4*>(rec + gid) + 3);
+  __device__ __forceinline__ uint32_t payload(int k) const { return st->gid[k]; }
+  __device__ __forceinline__ void blend_new(float a, const EvalState& ev) {
+    const float4 c = __ldg(reinterpret_cast<const float4*>(rec + st->gid[ev.k]) + 3);
     float dal, w;
     if (!composite(a, c, dal, w)) return;
     const float G = __expf(-0.5f * ev.rho2);
-    const float raw = c.w * G;
+    const float raw = st->a[ev.k].w * G;
     if (raw < kAlphaMax) {
       const float drho2 = -0.5f * dal * raw;
       const float sn = 2.0f * drho2 * ev.inv;
@@ -186,7 +190,7 @@ struct BackwardBlend {
         sacc[i * kTilePixels + t] = 0.0f;
       }
       if (nz) {
-        const uint32_t gid = vals[b0 + t];
+        const uint32_t gid = st->gid[t];
         const float4* r = reinterpret_cast<const float4*>(rec + gid);
         const float4 t1 = __ldg(r + 0), t2 = __ldg(r + 1), t3 = __ldg(r + 2);
         const float3 T3 = f3(t3.x, t3.y, t3.z);
@@ -222,17 +226,19 @@ struct BackwardBlend {
 __global__ void __launch_bounds__(kTilePixels, 2)
 render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
                        const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
-                       const FrameConst* __restrict__ fcp, const float* __restrict__ rgb,
+                       const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
+                       const float* __restrict__ rgb,
                        const float* __restrict__ drgb, const float* __restrict__ dalpha,
                        const float* __restrict__ final_T, const uint32_t* __restrict__ n_blended,
                        float4* __restrict__ grad, unsigned long long* __restrict__ stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem& s = *reinterpret_cast<TileSmem*>(smem_raw);
-  float* sacc = reinterpret_cast<float*>(smem_raw + kTileSmemBytes);
+  TileSmem<IndexQueue>& s = *reinterpret_cast<TileSmem<IndexQueue>*>(smem_raw);
+  float* sacc = reinterpret_cast<float*>(smem_raw + kStageBytes);
   const FrameConst fc = *fcp;
   const int tile = blockIdx.x;
   const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
-  const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+  int lx, ly;
+  tile_pixel(threadIdx.x, lx, ly);
   const int px = tx * kTile + lx, py = ty * kTile + ly;
   const bool in_image = px < fc.W && py < fc.H;
   const size_t HW = (size_t)fc.W * fc.H;
@@ -240,6 +246,7 @@ render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restr
   for (int i = threadIdx.x; i < kMoments * kTilePixels; i += kTilePixels) sacc[i] = 0.0f;
 
   BackwardBlend bl;
+  bl.st = &s.st;
   bl.rec = rec;
   bl.grad = grad;
   bl.fc = &fc;
@@ -275,7 +282,7 @@ render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restr
   unsigned long long neval = 0;
   uint32_t nmis = 0;
   __syncthreads();
-  traverse_tile<true>(s, ranges[tile], keys, vals, rec, fc, tx, ty, bl.x, bl.y, bl, neval, nmis);
+  traverse_tile<true>(s, ranges[tile], keys, vals, rec, aux, fc, tx, ty, bl.x, bl.y, bl, neval, nmis);
   // the replay must reproduce the forward blend count
   const bool mismatch = in_image && bl.nblend != n_blended[p];
   const unsigned ball = __ballot_sync(0xffffffffu, mismatch);
@@ -511,7 +518,7 @@ aaag_status launch_render_backward(const SceneDev& s, aaag_workspace* ws, const 
   prepare_backward_kernels();
   const int alt = ws->sorted_in_alt;
   render_backward_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kBackwardSmemBytes, st>>>(
-      ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->fc_dev, rgb, drgb, dalpha, ws->final_T,
+      ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->aux, ws->fc_dev, rgb, drgb, dalpha, ws->final_T,
       ws->n_blended, ws->grad_acc, ws->stats);
   aaag_status e = check_launch("render_backward");
   if (e != AAAG_OK || s.n == 0) return e;

@@ -212,10 +212,14 @@ cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
         const float tau = inflate_tau(fabsf(tau_signed));
         const float xlo = (float)(tx * kTile), ylo = (float)(ty * kTile);
         const float xhi = xlo + kTile, yhi = ylo + kTile;
-        // negative tau: the front of the ellipsoid reaches z_near
-        keep = tau_signed < 0.0f
-                   ? frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, xlo, xhi, ylo, yhi, tau)
-                   : frustum_hit<false>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, xlo, xhi, ylo, yhi, tau);
+        if (tau_signed < 0.0f) {
+          // the front of the ellipsoid reaches z_near: frustum truncated there
+          keep = frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, xlo, xhi, ylo, yhi, tau);
+        } else {
+          ConicTester ct;
+          ct.init(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, tau);
+          keep = ct.hit(xlo, ylo, xhi, yhi);
+        }
       }
       ++tested;
     }

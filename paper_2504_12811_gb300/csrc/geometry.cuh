@@ -130,16 +130,93 @@ __device__ __forceinline__ bool frustum_hit(float4 t1, float4 t2, float4 t3, flo
   return false;
 }
 
+// Tile test for a Gaussian whose tau-ellipsoid lies entirely beyond the near
+// plane (so in front of the camera).  A screen point (x, y) sees the
+// Gaussian's maximum below tau exactly where
+//     F(x, y) = |num(x, y)|^2 - tau |d(x, y)|^2 <= 0,
+// with num = h1 n2 - h2 n1 and d = n1 x n2 the affine functions of the pixel
+// planes of Eq. 4-5 (rho^2 = |num|^2 / |d|^2).  This region is the
+// ellipsoid's silhouette, a convex ellipse, so min over the frustum of rho^2 <
+// tau (Eq. 18) holds iff the tile rectangle meets it: iff the projected mean
+// (rho = 0) lies in the tile or F <= 0 somewhere on one of the four edges.  F
+// along an edge is a convex quadratic in the edge parameter, minimised at a
+// clamped vertex.  Uniform work, no square roots; same decision as the
+// frustum minimum up to rounding.
+struct ConicTester {
+  float3 Nx, Ny, Dx, Dy;   // d num/dx, d num/dy, d d/dx, d d/dy
+  float4 t1, t2, t3;
+  float fx, fy, cx, cy, tau, ax, ay, mx, my;
+
+  __device__ __forceinline__ void init(float4 t1_, float4 t2_, float4 t3_, float fx_, float fy_, float cx_,
+                                       float cy_, float tau_) {
+    t1 = t1_;
+    t2 = t2_;
+    t3 = t3_;
+    fx = fx_;
+    fy = fy_;
+    cx = cx_;
+    cy = cy_;
+    tau = tau_;
+    // planes at x = 0, y = 0: U = fx t1 + cx t3, W = fy t2 + cy t3
+    const float3 T3 = f3(t3.x, t3.y, t3.z);
+    const float3 Uv = f3(fx * t1.x + cx * t3.x, fx * t1.y + cx * t3.y, fx * t1.z + cx * t3.z);
+    const float Uw = fx * t1.w + cx * t3.w;
+    const float3 Wv = f3(fy * t2.x + cy * t3.x, fy * t2.y + cy * t3.y, fy * t2.z + cy * t3.z);
+    const float Ww = fy * t2.w + cy * t3.w;
+    Nx = Ww * T3 - t3.w * Wv;
+    Ny = t3.w * Uv - Uw * T3;
+    Dx = cross3(Wv, T3);
+    Dy = cross3(T3, Uv);
+    ax = dot3(Nx, Nx) - tau * dot3(Dx, Dx);
+    ay = dot3(Ny, Ny) - tau * dot3(Dy, Dy);
+    mx = fx * t1.w / t3.w + cx;   // projected mean
+    my = fy * t2.w / t3.w + cy;
+  }
+
+  // min over t in [0, len] of F(p + t e) = a t^2 + 2 b t + c <= 0, with
+  // num(p) = n, d(p) = d: the minimum is at an end or at the clamped vertex
+  __device__ __forceinline__ bool edge(float3 n, float3 d, float3 En, float3 Ed, float a, float len) const {
+    const float b = dot3(n, En) - tau * dot3(d, Ed);
+    const float c = dot3(n, n) - tau * dot3(d, d);
+    float m = fminf(c, fmaf(fmaf(a, len, 2.0f * b), len, c));
+    if (a > 0.0f) {
+      const float t = fminf(fmaxf(-b / a, 0.0f), len);
+      m = fminf(m, fmaf(fmaf(a, t, 2.0f * b), t, c));
+    }
+    return m <= 0.0f;
+  }
+
+  __device__ __forceinline__ bool hit(float x0, float y0, float x1, float y1) const {
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
+    // num and d at the corner (x0, y0), from the planes of that corner
+    const float3 T3 = f3(t3.x, t3.y, t3.z);
+    const float cxm = cx - x0, cym = cy - y0;
+    const float3 Uv = f3(fmaf(cxm, t3.x, fx * t1.x), fmaf(cxm, t3.y, fx * t1.y), fmaf(cxm, t3.z, fx * t1.z));
+    const float Uw = fmaf(cxm, t3.w, fx * t1.w);
+    const float3 Wv = f3(fmaf(cym, t3.x, fy * t2.x), fmaf(cym, t3.y, fy * t2.y), fmaf(cym, t3.z, fy * t2.z));
+    const float Ww = fmaf(cym, t3.w, fy * t2.w);
+    const float3 n00 = Uw * Wv - Ww * Uv;
+    const float3 d00 = cross3(Uv, Wv);
+    const float w = x1 - x0, h = y1 - y0;
+    const float3 n10 = n00 + w * Nx, d10 = d00 + w * Dx;
+    const float3 n01 = n00 + h * Ny, d01 = d00 + h * Dy;
+    return edge(n00, d00, Ny, Dy, ay, h) || edge(n10, d10, Ny, Dy, ay, h) || edge(n00, d00, Nx, Dx, ax, w) ||
+           edge(n01, d01, Nx, Dx, ax, w);
+  }
+};
+
 // Cutoff used by the conservative geometric tests: tau slightly inflated so
 // that float32 rounding never drops a tile or a Gaussian with alpha >= 1/255.
 __device__ __forceinline__ float inflate_tau(float tau) { return tau * (1.0f + 1e-4f) + 1e-4f; }
 
-// Decode the tile rectangle from the aux word.
+// The aux word holds the inclusive pixel-centre ranges [x0, x1] x [y0, y1]
+// (16 bits each) of a visible Gaussian; its tile rectangle is the tiles
+// holding those pixels.
 __device__ __forceinline__ void unpack_rect(uint4 a, int& tx0, int& ty0, int& tx1, int& ty1) {
-  tx0 = (int)(a.x & 0xffffu);
-  ty0 = (int)(a.x >> 16);
-  tx1 = (int)(a.y & 0xffffu);
-  ty1 = (int)(a.y >> 16);
+  tx0 = (int)(a.x & 0xffffu) / kTile;
+  ty0 = (int)(a.x >> 16) / kTile;
+  tx1 = (int)(a.y & 0xffffu) / kTile;
+  ty1 = (int)(a.y >> 16) / kTile;
 }
 
 }  // namespace aaag

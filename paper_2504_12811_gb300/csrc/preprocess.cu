@@ -104,13 +104,16 @@ __device__ __forceinline__ bool axis_bounds(float3 Ai, float3 A3, float mi, floa
   return true;
 }
 
-__device__ __forceinline__ bool tile_range(float p1, float p2, int size, int ntiles, int& t0, int& t1) {
-  if (!(p2 >= 0.0f) || !(p1 <= (float)size)) return false;
-  p1 = fmaxf(p1, 0.0f);
-  p2 = fminf(p2, (float)size);
-  t0 = (int)floorf(p1 * (1.0f / kTile));
-  t1 = min((int)floorf(p2 * (1.0f / kTile)), ntiles - 1);
-  return t0 <= t1;
+// Pixels whose centre (i + 1/2) lies in the screen interval [p1, p2],
+// clamped to the image: the only pixels of this axis that can see the
+// Gaussian.  Returns false when there is none.
+__device__ __forceinline__ bool pixel_range(float p1, float p2, int size, int& i0, int& i1) {
+  const float lo = fmaxf(p1 - 0.5f, 0.0f);
+  const float hi = fminf(p2 - 0.5f, (float)(size - 1));
+  if (!(lo <= hi)) return false;   // also rejects NaN bounds
+  i0 = (int)ceilf(lo);
+  i1 = (int)floorf(hi);
+  return i0 <= i1;
 }
 
 __global__ void __launch_bounds__(256)
@@ -159,124 +162,138 @@ preprocess_kernel(SceneDev s, const FrameConst* __restrict__ fcp, Record* __rest
     }
     const float s2x = sx * sx, s2y = sy * sy, s2z = sz * sz;
     const float hx = s2x + kv, hy = s2y + kv, hz = s2z + kv;
-    // d = unit vector camera -> mean; d' = R^T d
-    const float dx0 = mx - fc.o[0], dy0 = my - fc.o[1], dz0 = mz - fc.o[2];
-    const float dist = sqrtf(dx0 * dx0 + dy0 * dy0 + dz0 * dz0);
-    const float idist = 1.0f / dist;
-    const float ddx = dx0 * idist, ddy = dy0 * idist, ddz = dz0 * idist;
-    const float p0 = R[0] * ddx + R[3] * ddy + R[6] * ddz;
-    const float p1 = R[1] * ddx + R[4] * ddy + R[7] * ddz;
-    const float p2 = R[2] * ddx + R[5] * ddy + R[8] * ddz;
-    // Eq. 12 divided through by s_hat_1 s_hat_2 s_hat_3: a weighted mean of
-    // r_j r_k with weights d'_i^2 / s_hat_i, r_j = s_j^2 / s_hat_j
-    const float w0 = p0 * p0 / hx, w1 = p1 * p1 / hy, w2 = p2 * p2 / hz;
-    const float r0 = s2x / hx, r1 = s2y / hy, r2 = s2z / hz;
-    const float phi2 = (w0 * r1 * r2 + w1 * r0 * r2 + w2 * r0 * r1) / (w0 + w1 + w2);
-    const float o_hat = opac * sqrtf(phi2);
+    // Conservative early reject.  The tau-ellipsoid lies inside the sphere
+    // of radius sqrt(tau_max * max_i s_hat_i^2) around the mean, where
+    // tau_max = 2 ln(255 o) >= tau because the amplitude factor of Eq. 12 is
+    // at most 1.  A sphere wholly outside one side plane of the image frustum
+    // or in front of z_near holds no visible point, and the remaining work is
+    // skipped (most Gaussians of a large scene are outside the view).
+    const float tau_max = 2.0f * logf(fmaxf(opac * 255.0f, 1.0f));
+    const float rad = fmaf(sqrtf(inflate_tau(tau_max) * fmaxf(hx, fmaxf(hy, hz))), 1.001f, 1e-6f);
+    bool near_view = vz + rad >= fc.znear && opac > kAlphaMin;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      near_view &= fmaf(fc.side[j][0], vx, fmaf(fc.side[j][1], vy, fc.side[j][2] * vz)) >= -rad;
+    if (near_view) {
+      // d = unit vector camera -> mean; d' = R^T d
+      const float dx0 = mx - fc.o[0], dy0 = my - fc.o[1], dz0 = mz - fc.o[2];
+      const float dist = sqrtf(dx0 * dx0 + dy0 * dy0 + dz0 * dz0);
+      const float idist = 1.0f / dist;
+      const float ddx = dx0 * idist, ddy = dy0 * idist, ddz = dz0 * idist;
+      const float p0 = R[0] * ddx + R[3] * ddy + R[6] * ddz;
+      const float p1 = R[1] * ddx + R[4] * ddy + R[7] * ddz;
+      const float p2 = R[2] * ddx + R[5] * ddy + R[8] * ddz;
+      // Eq. 12 divided through by s_hat_1 s_hat_2 s_hat_3: a weighted mean of
+      // r_j r_k with weights d'_i^2 / s_hat_i, r_j = s_j^2 / s_hat_j
+      const float w0 = p0 * p0 / hx, w1 = p1 * p1 / hy, w2 = p2 * p2 / hz;
+      const float r0 = s2x / hx, r1 = s2y / hy, r2 = s2z / hz;
+      const float phi2 = (w0 * r1 * r2 + w1 * r0 * r2 + w2 * r0 * r1) / (w0 + w1 + w2);
+      const float o_hat = opac * sqrtf(phi2);
 
-    if (o_hat > kAlphaMin) {
-      const float tau = 2.0f * logf(o_hat * 255.0f);
-      const float spx = sqrtf(hx), spy = sqrtf(hy), spz = sqrtf(hz);
-      // camera origin in normalised Gaussian space: S'^-1 R^T (o - mu)
-      const float ux = -dist * p0 / spx, uy = -dist * p1 / spy, uz = -dist * p2 / spz;
-      const bool inside = ux * ux + uy * uy + uz * uz < tau;
-      // A = Rv R S': rows are the view axes expressed in the Gaussian frame
-      float A[9];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float a0 = fc.Rv[3 * r + 0] * R[0] + fc.Rv[3 * r + 1] * R[3] + fc.Rv[3 * r + 2] * R[6];
-        const float a1 = fc.Rv[3 * r + 0] * R[1] + fc.Rv[3 * r + 1] * R[4] + fc.Rv[3 * r + 2] * R[7];
-        const float a2 = fc.Rv[3 * r + 0] * R[2] + fc.Rv[3 * r + 1] * R[5] + fc.Rv[3 * r + 2] * R[8];
-        A[3 * r + 0] = a0 * spx;
-        A[3 * r + 1] = a1 * spy;
-        A[3 * r + 2] = a2 * spz;
-      }
-      const float3 A1 = f3(A[0], A[1], A[2]), A2 = f3(A[3], A[4], A[5]), A3 = f3(A[6], A[7], A[8]);
-      const float tau_c = inflate_tau(tau);
-      const float zext = sqrtf(tau_c * dot3(A3, A3));
-      const float z_lo = vz - zext, z_hi = vz + zext;
-      int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
-      bool ok = !inside && z_hi >= fc.znear;
-      if (ok) {
-        float px1, px2, py1, py2;
-        ok = axis_bounds(A1, A3, vx, vz, tau_c, fc.fx, fc.cx, fc.eps, px1, px2) &&
-             axis_bounds(A2, A3, vy, vz, tau_c, fc.fy, fc.cy, fc.eps, py1, py2) &&
-             tile_range(px1, px2, fc.W, fc.tiles_x, tx0, tx1) &&
-             tile_range(py1, py2, fc.H, fc.tiles_y, ty0, ty1);
-      }
-      const float4 t1 = make_float4(A[0], A[1], A[2], vx);
-      const float4 t2 = make_float4(A[3], A[4], A[5], vy);
-      const float4 t3 = make_float4(A[6], A[7], A[8], vz);
-      if (ok) {
-        // whole-image frustum cull (Sec. 3.4, last paragraph)
-        const float W = (float)fc.W, H = (float)fc.H;
-        ok = (z_lo < fc.znear)
-                 ? frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, 0.f, W, 0.f, H, tau_c)
-                 : frustum_hit<false>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, 0.f, W, 0.f, H, tau_c);
-      }
-      if (ok) {
-        visible = true;
-        // colour (view-dependent, real SH up to degree 3)
-        const int K = (s.sh_degree + 1) * (s.sh_degree + 1);
-        float Y[16];
-        sh_basis(ddx, ddy, ddz, s.sh_degree, Y);
-        float cr = 0.5f, cg = 0.5f, cb = 0.5f;
-        const float* shp = s.sh + (size_t)i * K * 3;
-        if (K == 16) {
-          const float4* s4 = reinterpret_cast<const float4*>(shp);
-          float c[48];
-#pragma unroll
-          for (int j = 0; j < 12; ++j) {
-            const float4 v = s4[j];
-            c[4 * j + 0] = v.x; c[4 * j + 1] = v.y; c[4 * j + 2] = v.z; c[4 * j + 3] = v.w;
-          }
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            cr += Y[j] * c[3 * j + 0];
-            cg += Y[j] * c[3 * j + 1];
-            cb += Y[j] * c[3 * j + 2];
-          }
-        } else {
-          for (int j = 0; j < K; ++j) {
-            cr += Y[j] * shp[3 * j + 0];
-            cg += Y[j] * shp[3 * j + 1];
-            cb += Y[j] * shp[3 * j + 2];
-          }
+      if (o_hat > kAlphaMin) {
+        const float tau = 2.0f * logf(o_hat * 255.0f);
+        const float spx = sqrtf(hx), spy = sqrtf(hy), spz = sqrtf(hz);
+        // camera origin in normalised Gaussian space: S'^-1 R^T (o - mu)
+        const float ux = -dist * p0 / spx, uy = -dist * p1 / spy, uz = -dist * p2 / spz;
+        const bool inside = ux * ux + uy * uy + uz * uz < tau;
+        // A = Rv R S': rows are the view axes expressed in the Gaussian frame
+        float A[9];
+  #pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const float a0 = fc.Rv[3 * r + 0] * R[0] + fc.Rv[3 * r + 1] * R[3] + fc.Rv[3 * r + 2] * R[6];
+          const float a1 = fc.Rv[3 * r + 0] * R[1] + fc.Rv[3 * r + 1] * R[4] + fc.Rv[3 * r + 2] * R[7];
+          const float a2 = fc.Rv[3 * r + 0] * R[2] + fc.Rv[3 * r + 1] * R[5] + fc.Rv[3 * r + 2] * R[8];
+          A[3 * r + 0] = a0 * spx;
+          A[3 * r + 1] = a1 * spy;
+          A[3 * r + 2] = a2 * spz;
         }
-        Record out;
-        out.t1 = t1;
-        out.t2 = t2;
-        out.t3 = t3;
-        out.rgba = make_float4(fmaxf(cr, 0.0f), fmaxf(cg, 0.0f), fmaxf(cb, 0.0f), o_hat);
-        rec[i] = out;
-        // Depth key: a lower bound of the depth t* of the maximum on every
-        // contributing ray.  In normalised Gaussian space the maximum u* of a
-        // ray from the camera c is the foot of the perpendicular from the
-        // origin, so u*.(u* - c) = 0: u* lies on the sphere |u|^2 = u.c, and
-        // contributing means |u*|^2 <= tau.  Hence u*.c_hat is in
-        // [0, tau/|c|] and the part of u* orthogonal to c_hat has length
-        // <= sqrt(tau); the view depth Z = A3.u + mu_z is then at least
-        //   mu_z - sqrt(tau) |A3_perp| + min(0, A3.c_hat) tau / |c|,
-        // with A3_perp the part of A3 orthogonal to c_hat.  This is never
-        // below the front of the tau-ellipsoid (|A3_perp| <= |A3|) and is much
-        // tighter for Gaussians seen head-on.  Quantised max(bound, znear),
-        // rounded down.
-        const float cn = sqrtf(ux * ux + uy * uy + uz * uz);
-        const float3 ch = (1.0f / cn) * f3(ux, uy, uz);
-        const float a3c = dot3(A3, ch);
-        const float3 A3p = A3 - a3c * ch;
-        float t_lo = vz - sqrtf(tau_c * dot3(A3p, A3p)) + fminf(a3c, 0.0f) * tau_c / cn;
-        t_lo -= 1e-5f * fabsf(t_lo) + 1e-6f;
-        const float zk = fmaxf(fmaxf(t_lo, z_lo), fc.znear);
-        uint32_t dk = (__float_as_uint(zk) - fc.znear_bits) >> fc.depth_shift;
-        const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
-        dk = min(dk, dmax);
-        // tau_rho, negated when the front of the ellipsoid reaches znear (the
-        // tile test then truncates the frustum at the near plane)
-        aux[i] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16),
-                            __float_as_uint(z_lo < fc.znear ? -tau : tau), dk);
-        const uint32_t ntiles = (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1);
-        chunks[i] = (ntiles + 31u) / 32u;
+        const float3 A1 = f3(A[0], A[1], A[2]), A2 = f3(A[3], A[4], A[5]), A3 = f3(A[6], A[7], A[8]);
+        const float tau_c = inflate_tau(tau);
+        const float zext = sqrtf(tau_c * dot3(A3, A3));
+        const float z_lo = vz - zext, z_hi = vz + zext;
+        int ix0 = 1, ix1 = 0, iy0 = 1, iy1 = 0;   // pixel-centre ranges
+        bool ok = !inside && z_hi >= fc.znear;
+        if (ok) {
+          float px1, px2, py1, py2;
+          ok = axis_bounds(A1, A3, vx, vz, tau_c, fc.fx, fc.cx, fc.eps, px1, px2) &&
+               axis_bounds(A2, A3, vy, vz, tau_c, fc.fy, fc.cy, fc.eps, py1, py2) &&
+               pixel_range(px1, px2, fc.W, ix0, ix1) && pixel_range(py1, py2, fc.H, iy0, iy1);
+        }
+        const float4 t1 = make_float4(A[0], A[1], A[2], vx);
+        const float4 t2 = make_float4(A[3], A[4], A[5], vy);
+        const float4 t3 = make_float4(A[6], A[7], A[8], vz);
+        if (ok) {
+          // whole-image frustum cull (Sec. 3.4, last paragraph)
+          const float W = (float)fc.W, H = (float)fc.H;
+          ok = (z_lo < fc.znear)
+                   ? frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, 0.f, W, 0.f, H, tau_c)
+                   : frustum_hit<false>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, 0.f, W, 0.f, H, tau_c);
+        }
+        if (ok) {
+          visible = true;
+          // colour (view-dependent, real SH up to degree 3)
+          const int K = (s.sh_degree + 1) * (s.sh_degree + 1);
+          float Y[16];
+          sh_basis(ddx, ddy, ddz, s.sh_degree, Y);
+          float cr = 0.5f, cg = 0.5f, cb = 0.5f;
+          const float* shp = s.sh + (size_t)i * K * 3;
+          if (K == 16) {
+            const float4* s4 = reinterpret_cast<const float4*>(shp);
+            float c[48];
+  #pragma unroll
+            for (int j = 0; j < 12; ++j) {
+              const float4 v = s4[j];
+              c[4 * j + 0] = v.x; c[4 * j + 1] = v.y; c[4 * j + 2] = v.z; c[4 * j + 3] = v.w;
+            }
+  #pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              cr += Y[j] * c[3 * j + 0];
+              cg += Y[j] * c[3 * j + 1];
+              cb += Y[j] * c[3 * j + 2];
+            }
+          } else {
+            for (int j = 0; j < K; ++j) {
+              cr += Y[j] * shp[3 * j + 0];
+              cg += Y[j] * shp[3 * j + 1];
+              cb += Y[j] * shp[3 * j + 2];
+            }
+          }
+          Record out;
+          out.t1 = t1;
+          out.t2 = t2;
+          out.t3 = t3;
+          out.rgba = make_float4(fmaxf(cr, 0.0f), fmaxf(cg, 0.0f), fmaxf(cb, 0.0f), o_hat);
+          rec[i] = out;
+          // Depth key: a lower bound of the depth t* of the maximum on every
+          // contributing ray.  In normalised Gaussian space the maximum u* of a
+          // ray from the camera c is the foot of the perpendicular from the
+          // origin, so u*.(u* - c) = 0: u* lies on the sphere |u|^2 = u.c, and
+          // contributing means |u*|^2 <= tau.  Hence u*.c_hat is in
+          // [0, tau/|c|] and the part of u* orthogonal to c_hat has length
+          // <= sqrt(tau); the view depth Z = A3.u + mu_z is then at least
+          //   mu_z - sqrt(tau) |A3_perp| + min(0, A3.c_hat) tau / |c|,
+          // with A3_perp the part of A3 orthogonal to c_hat.  This is never
+          // below the front of the tau-ellipsoid (|A3_perp| <= |A3|) and is much
+          // tighter for Gaussians seen head-on.  Quantised max(bound, znear),
+          // rounded down.
+          const float cn = sqrtf(ux * ux + uy * uy + uz * uz);
+          const float3 ch = (1.0f / cn) * f3(ux, uy, uz);
+          const float a3c = dot3(A3, ch);
+          const float3 A3p = A3 - a3c * ch;
+          float t_lo = vz - sqrtf(tau_c * dot3(A3p, A3p)) + fminf(a3c, 0.0f) * tau_c / cn;
+          t_lo -= 1e-5f * fabsf(t_lo) + 1e-6f;
+          const float zk = fmaxf(fmaxf(t_lo, z_lo), fc.znear);
+          uint32_t dk = (__float_as_uint(zk) - fc.znear_bits) >> fc.depth_shift;
+          const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
+          dk = min(dk, dmax);
+          // tau_rho, negated when the front of the ellipsoid reaches znear (the
+          // tile test then truncates the frustum at the near plane)
+          aux[i] = make_uint4((uint32_t)ix0 | ((uint32_t)iy0 << 16), (uint32_t)ix1 | ((uint32_t)iy1 << 16),
+                              __float_as_uint(z_lo < fc.znear ? -tau : tau), dk);
+          const uint32_t ntiles = (uint32_t)((ix1 / kTile) - (ix0 / kTile) + 1) *
+                                  (uint32_t)((iy1 / kTile) - (iy0 / kTile) + 1);
+          chunks[i] = (ntiles + 31u) / 32u;
+        }
       }
     }
     if (!visible) {

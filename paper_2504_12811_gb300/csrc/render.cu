@@ -27,10 +27,13 @@ namespace aaag {
 namespace {
 
 struct ForwardBlend {
+  using Queue = IndexQueue;
+  const StageSmem* st;
   const Record* rec;
   float T, Cr, Cg, Cb;
   bool done;
   uint32_t nblend;
+  // blend Gaussian gid with opacity a (its colour is read from its record)
   __device__ __forceinline__ void blend(float a, uint32_t gid) {
     const float Tn = T * (1.0f - a);
     if (Tn < kTStop) {
@@ -45,22 +48,26 @@ struct ForwardBlend {
     T = Tn;
     ++nblend;
   }
-  __device__ __forceinline__ void blend_new(float a, uint32_t gid, const EvalState&) { blend(a, gid); }
+  __device__ __forceinline__ uint32_t payload(int k) const { return st->gid[k]; }
+  __device__ __forceinline__ void blend_new(float a, const EvalState& ev) { blend(a, st->gid[ev.k]); }
 };
 
 // Render one tile of one frame (all threads of the block).
-__device__ __forceinline__ void render_tile(TileSmem& s, int tile, const uint2* __restrict__ ranges,
+__device__ __forceinline__ void render_tile(TileSmem<IndexQueue>& s, int tile, const uint2* __restrict__ ranges,
                                            const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                                           const Record* __restrict__ rec, const FrameConst& fc,
+                                           const Record* __restrict__ rec, const uint4* __restrict__ aux,
+                                           const FrameConst& fc,
                                            float* __restrict__ rgb, float* __restrict__ alpha,
                                            float* __restrict__ final_T, uint32_t* __restrict__ n_blended,
                                            unsigned long long* __restrict__ stats) {
   const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
-  const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+  int lx, ly;
+  tile_pixel(threadIdx.x, lx, ly);
   const int px = tx * kTile + lx, py = ty * kTile + ly;
   const bool in_image = px < fc.W && py < fc.H;
 
   ForwardBlend bl;
+  bl.st = &s.st;
   bl.rec = rec;
   bl.T = 1.0f;
   bl.Cr = bl.Cg = bl.Cb = 0.0f;
@@ -68,7 +75,7 @@ __device__ __forceinline__ void render_tile(TileSmem& s, int tile, const uint2* 
   bl.nblend = 0;
   unsigned long long neval = 0;
   uint32_t nmis = 0;
-  traverse_tile<false>(s, ranges[tile], keys, vals, rec, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f, bl,
+  traverse_tile<false>(s, ranges[tile], keys, vals, rec, aux, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f, bl,
                        neval, nmis);
 
   if (in_image) {
@@ -97,13 +104,13 @@ __device__ __forceinline__ void render_tile(TileSmem& s, int tile, const uint2* 
 
 __global__ void __launch_bounds__(kTilePixels, 3)
 render_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
-              const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
+              const uint32_t* __restrict__ vals, const Record* __restrict__ rec, const uint4* __restrict__ aux,
               const FrameConst* __restrict__ fcp, float* __restrict__ rgb, float* __restrict__ alpha,
               float* __restrict__ final_T, uint32_t* __restrict__ n_blended, unsigned long long* __restrict__ stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem& s = *reinterpret_cast<TileSmem*>(smem_raw);
+  TileSmem<IndexQueue>& s = *reinterpret_cast<TileSmem<IndexQueue>*>(smem_raw);
   const FrameConst fc = *fcp;
-  render_tile(s, blockIdx.x, ranges, keys, vals, rec, fc, rgb, alpha, final_T, n_blended, stats);
+  render_tile(s, blockIdx.x, ranges, keys, vals, rec, aux, fc, rgb, alpha, final_T, n_blended, stats);
 }
 
 // ---- K8: one persistent launch over the tiles of several frames.
@@ -115,6 +122,7 @@ struct RenderJob {
   const uint32_t* keys;
   const uint32_t* vals;
   const Record* rec;
+  const uint4* aux;
   const FrameConst* fc;
   float* rgb;
   float* alpha;
@@ -134,7 +142,7 @@ struct RenderBatch {
 __global__ void __launch_bounds__(kTilePixels, 3)
 serve_render_kernel(const __grid_constant__ RenderBatch b, uint32_t* __restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem& s = *reinterpret_cast<TileSmem*>(smem_raw);
+  TileSmem<IndexQueue>& s = *reinterpret_cast<TileSmem<IndexQueue>*>(smem_raw);
   __shared__ uint32_t s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
@@ -146,7 +154,7 @@ serve_render_kernel(const __grid_constant__ RenderBatch b, uint32_t* __restrict_
     while (j + 1 < b.n && b.job[j + 1].first <= item) ++j;
     const RenderJob& J = b.job[j];
     const FrameConst fc = *J.fc;
-    render_tile(s, (int)(item - J.first), J.ranges, J.keys, J.vals, J.rec, fc, J.rgb, J.alpha, J.final_T,
+    render_tile(s, (int)(item - J.first), J.ranges, J.keys, J.vals, J.rec, J.aux, fc, J.rgb, J.alpha, J.final_T,
                 J.n_blended, J.stats);
   }
 }
@@ -158,12 +166,12 @@ int g_serve_blocks = 0;
 void prepare_render_kernels() {
   static bool done = false;
   if (done) return;
-  cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
-  cudaFuncSetAttribute(serve_render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemBytes);
+  cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kForwardSmemBytes);
+  cudaFuncSetAttribute(serve_render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kForwardSmemBytes);
   int dev = 0, sms = 1, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_render_kernel, kTilePixels, kTileSmemBytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_render_kernel, kTilePixels, kForwardSmemBytes);
   g_serve_blocks = std::max(1, sms) * std::max(1, per_sm);
   done = true;
 }
@@ -182,6 +190,7 @@ aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, fl
     J.keys = w->keys[alt];
     J.vals = w->vals[alt];
     J.rec = w->records;
+    J.aux = w->aux;
     J.fc = w->fc_dev;
     J.rgb = rgb[i];
     J.alpha = alpha[i];
@@ -197,15 +206,15 @@ aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, fl
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws[0]->stats + kStatBatchCounter);
   if (cudaMemsetAsync(counter, 0, 4, st) != cudaSuccess) return check_launch("render_batch memset");
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g_serve_blocks, total));
-  serve_render_kernel<<<grid, kTilePixels, kTileSmemBytes, st>>>(b, counter);
+  serve_render_kernel<<<grid, kTilePixels, kForwardSmemBytes, st>>>(b, counter);
   return check_launch("serve_render");
 }
 
 aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st) {
   prepare_render_kernels();
   const int alt = ws->sorted_in_alt;
-  render_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kTileSmemBytes, st>>>(ws->ranges, ws->keys[alt], ws->vals[alt],
-                                                               ws->records, ws->fc_dev, rgb, alpha, ws->final_T,
+  render_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kForwardSmemBytes, st>>>(ws->ranges, ws->keys[alt], ws->vals[alt],
+                                                               ws->records, ws->aux, ws->fc_dev, rgb, alpha, ws->final_T,
                                                                ws->n_blended, ws->stats);
   return check_launch("render");
 }

@@ -25,9 +25,21 @@
 //   3. otherwise it is inserted into the pixel's sorted queue.
 // The result is the exact (t*, arrival) order as long as the queue does not
 // overflow; on overflow the nearer of the queue front and the new entry is
-// blended early and counted as a potential misorder.  The queue is a per-thread
-// ring buffer in shared memory laid out [slot][thread] (bank-conflict free):
-// O(1) pop, insertion by shifting from the tail.
+// blended early and counted as a potential misorder.  Queue entries stay in
+// fixed per-thread slots in shared memory, laid out [slot][thread] (bank-
+// conflict free); their order lives in one 64-bit register holding the slot
+// numbers nearest first, 4 bits each, so an insertion moves no entry (a scan
+// of depths from the far end, then a register shift) and a release reads one.
+// The front's depth stays in a register.  Shared memory per block is kept
+// at 74 KB so that three tile blocks fit on an SM: the traversal is bound by
+// latency, and resident warps are what hides it.
+//
+// Warp skipping.  Warp w of a tile block owns the 8x4 pixel block at
+// (8 (w & 1), 4 (w >> 1)).  When a Gaussian is staged, the pixel-centre ranges
+// from its view-space bounds (Eq. 14-17) give the set of warps holding a pixel
+// that can see it, as an 8-bit mask; the other warps skip it without
+// evaluating.  A skipped pixel could not contribute (its centre lies outside
+// the bounds), so the blends and their order are unchanged.
 #pragma once
 
 #include "aaag_internal.cuh"
@@ -36,18 +48,66 @@ namespace aaag {
 
 constexpr int kQueue = 16;   // per-pixel re-sort queue entries (power of two)
 
-struct TileSmem {
-  float4 a[kTilePixels];  // N0.xyz, o_hat
-  float4 b[kTilePixels];  // Nx.xyz, L_next: lower bound of t* for every later pair
-  float4 c[kTilePixels];  // Ny.xyz, tau+: |num|^2 > tau+ |d|^2 rules out alpha >= 1/255
-  float4 d[kTilePixels];  // D0.xyz, G.x
-  float4 e[kTilePixels];  // Dx.xyz, G.y
-  float4 f[kTilePixels];  // Dy.xyz, G.z
-  float qt[kQueue][kTilePixels];     // queued depth t*
-  float qa[kQueue][kTilePixels];     // queued alpha
-  uint32_t qg[kQueue][kTilePixels];  // queued Gaussian index
+// Coefficients of the staged Gaussians (one batch of pairs of one tile).
+struct StageSmem {
+  float4 a[kTilePixels];    // N0.xyz, o_hat
+  float4 b[kTilePixels];    // Nx.xyz, mask of the warps holding a pixel that can see it (bits)
+  float4 c[kTilePixels];    // Ny.xyz, tau+: |num|^2 > tau+ |d|^2 rules out alpha >= 1/255
+  float4 d[kTilePixels];    // D0.xyz, G.x
+  float4 e[kTilePixels];    // Dx.xyz, G.y
+  float4 f[kTilePixels];    // Dy.xyz, G.z
+  float L[kTilePixels];     // L_next: lower bound of t* for every later pair
+  uint32_t gid[kTilePixels];  // Gaussian index
 };
-constexpr size_t kTileSmemBytes = sizeof(TileSmem);
+
+// Queue store, [slot][thread], one array per field: (t*, alpha, Gaussian
+// index).  The Payload type is what an entry carries besides (t*, alpha).
+struct IndexQueue {
+  using Payload = uint32_t;
+  float t_[kQueue][kTilePixels];      // t*
+  float a_[kQueue][kTilePixels];      // alpha
+  uint32_t g_[kQueue][kTilePixels];   // Gaussian index
+  __device__ __forceinline__ float t(int s, int tid) const { return t_[s][tid]; }
+  __device__ __forceinline__ void load(int s, int tid, float& a, Payload& p) const {
+    a = a_[s][tid];
+    p = g_[s][tid];
+  }
+  __device__ __forceinline__ void put(int s, int tid, float t, float a, Payload p) {
+    t_[s][tid] = t;
+    a_[s][tid] = a;
+    g_[s][tid] = p;
+  }
+};
+
+template <class Q>
+struct TileSmem {
+  StageSmem st;
+  Q q;
+};
+constexpr size_t kForwardSmemBytes = sizeof(TileSmem<IndexQueue>);
+static_assert(3 * (kForwardSmemBytes + 1024) <= 228 * 1024, "three tile blocks per SM");
+
+// Tile-relative pixel of thread tid: warp w owns the 8x4 block at
+// (8 (w & 1), 4 (w >> 1)), lanes row-major inside it.
+__device__ __forceinline__ void tile_pixel(int tid, int& lx, int& ly) {
+  const int w = tid >> 5, lane = tid & 31;
+  lx = ((w & 1) << 3) | (lane & 7);
+  ly = ((w >> 1) << 2) | (lane >> 3);
+}
+
+// Warps of the tile at (ox, oy) that hold a pixel of the inclusive pixel
+// rectangle [x0, x1] x [y0, y1] packed in r (16 bits each), as a bit mask.
+__device__ __forceinline__ uint32_t warp_mask(uint2 r, int ox, int oy) {
+  const int x0 = max((int)(r.x & 0xffffu) - ox, 0), x1 = min((int)(r.y & 0xffffu) - ox, kTile - 1);
+  const int y0 = max((int)(r.x >> 16) - oy, 0), y1 = min((int)(r.y >> 16) - oy, kTile - 1);
+  if (x0 > x1 || y0 > y1) return 0u;
+  const uint32_t cols = (2u << (x1 >> 3)) - (1u << (x0 >> 3));   // warp columns 0..1
+  uint32_t m = 0u;
+#pragma unroll
+  for (int wy = 0; wy < 4; ++wy)
+    if (wy >= (y0 >> 2) && wy <= (y1 >> 2)) m |= cols << (2 * wy);
+  return m;
+}
 
 __device__ __forceinline__ float decode_depth(uint32_t key, const FrameConst& fc) {
   const uint32_t dk = key & ((fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u));
@@ -61,9 +121,11 @@ __device__ __forceinline__ float3 crs(float3 a, float3 b) {
   return f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
 }
 
-// Coefficients of one Gaussian for one tile (cxm = cx - x_t, cym = cy - y_t).
-__device__ __forceinline__ void stage_one(TileSmem& s, int slot, const Record* rec, uint32_t gid, float Lnext,
-                                          const FrameConst& fc, float cxm, float cym) {
+// Coefficients of one Gaussian for the tile at (ox, oy) (cxm = cx - ox,
+// cym = cy - oy); rect: its pixel-centre ranges.
+__device__ __forceinline__ void stage_one(StageSmem& s, int slot, const Record* rec, uint32_t gid, uint2 rect,
+                                          float Lnext, const FrameConst& fc, float cxm, float cym, int ox,
+                                          int oy) {
   const float4* r = reinterpret_cast<const float4*>(rec + gid);
   const float4 t1 = __ldg(r + 0), t2 = __ldg(r + 1), t3 = __ldg(r + 2), cw = __ldg(r + 3);
   const float3 T3 = f3(t3.x, t3.y, t3.z);
@@ -81,7 +143,8 @@ __device__ __forceinline__ void stage_one(TileSmem& s, int slot, const Record* r
   const float fxfy = fc.fx * fc.fy;
   const float3 G = fxfy * fma3(t1.w, crs(A2, T3), fma3(t2.w, crs(T3, A1), t3.w * crs(A1, A2)));
   s.a[slot] = make_float4(N0.x, N0.y, N0.z, cw.w);
-  s.b[slot] = make_float4(Nx.x, Nx.y, Nx.z, Lnext);
+  s.b[slot] = make_float4(Nx.x, Nx.y, Nx.z, __uint_as_float(warp_mask(rect, ox, oy)));
+  s.L[slot] = Lnext;
   // rho^2 <= tau_rho exactly where o_hat exp(-rho^2/2) >= 1/255; the margin
   // keeps the division-free prefilter conservative under float32 rounding
   const float tau = 2.0f * logf(cw.w * 255.0f);
@@ -89,37 +152,41 @@ __device__ __forceinline__ void stage_one(TileSmem& s, int slot, const Record* r
   s.d[slot] = make_float4(D0.x, D0.y, D0.z, G.x);
   s.e[slot] = make_float4(Dx.x, Dx.y, Dx.z, G.y);
   s.f[slot] = make_float4(Dy.x, Dy.y, Dy.z, G.z);
+  s.gid[slot] = gid;
 }
 
-// Per-thread sorted ring buffer in shared memory.
+// Per-thread sorted queue: entries in fixed slots, order in a register.
+template <class Q>
 struct SmemQueue {
-  TileSmem* s;
-  int tid, head, n;
-  __device__ __forceinline__ int slot(int i) const { return (head + i) & (kQueue - 1); }
-  __device__ __forceinline__ float front_t() const { return s->qt[head][tid]; }
-  __device__ __forceinline__ float front_a() const { return s->qa[head][tid]; }
-  __device__ __forceinline__ uint32_t front_g() const { return s->qg[head][tid]; }
-  __device__ __forceinline__ void pop() {
-    head = (head + 1) & (kQueue - 1);
-    --n;
+  static_assert(kQueue == 16, "the order word holds 16 four-bit slot numbers");
+  Q* q;
+  int tid, n;
+  unsigned long long order;   // nibble i: slot of the i-th nearest entry
+  uint32_t used;              // bit s: slot s holds an entry
+  float ft;                   // t* of the nearest entry (n > 0)
+  __device__ __forceinline__ int slot_at(int i) const { return (int)((order >> (4 * i)) & 15ull); }
+  // blend the nearest entry and remove it
+  template <class Blender>
+  __device__ __forceinline__ void release(Blender& bl) {
+    const int s = (int)(order & 15ull);
+    float a;
+    typename Q::Payload p;
+    q->load(s, tid, a, p);
+    bl.blend(a, p);
+    order >>= 4;
+    used &= ~(1u << s);
+    if (--n > 0) ft = q->t((int)(order & 15ull), tid);
   }
-  // sorted insert (n < kQueue); ties keep arrival order
-  __device__ __forceinline__ void insert(float t, float a, uint32_t g) {
+  // sorted insert (n < kQueue), after every entry with an equal t*
+  __device__ __forceinline__ void insert(float t, float a, typename Q::Payload p) {
     int i = n;
-    while (i > 0) {
-      const int p = slot(i - 1);
-      const float tp = s->qt[p][tid];
-      if (!(tp > t)) break;
-      const int q = slot(i);
-      s->qt[q][tid] = tp;
-      s->qa[q][tid] = s->qa[p][tid];
-      s->qg[q][tid] = s->qg[p][tid];
-      --i;
-    }
-    const int q = slot(i);
-    s->qt[q][tid] = t;
-    s->qa[q][tid] = a;
-    s->qg[q][tid] = g;
+    while (i > 0 && q->t(slot_at(i - 1), tid) > t) --i;
+    const int s = __ffs(~used) - 1;   // a free slot: fewer than 16 are used
+    used |= 1u << s;
+    q->put(s, tid, t, a, p);
+    const unsigned long long low = order & ((1ull << (4 * i)) - 1ull);   // 4 i <= 60
+    order = low | ((unsigned long long)s << (4 * i)) | ((order ^ low) << 4);
+    if (i == 0) ft = t;
     ++n;
   }
 };
@@ -132,41 +199,52 @@ struct EvalState {
 };
 
 // Traverse one tile for one pixel.  Blender must provide:
+//   using Queue;                                     its queue store
 //   bool done;                                       pixel finished
-//   void blend(float alpha, uint32_t gid);           blend a queued contributor
-//   void blend_new(float alpha, uint32_t gid, const EvalState&);
-//                                                    blend the staged Gaussian k
+//   void blend(float alpha, Queue::Payload);         blend a queued contributor
+//   void blend_new(float alpha, const EvalState&);   blend the staged Gaussian k
+//   Queue::Payload payload(int k);                   what a queued entry of k carries
 // With CONVERGENT, every lane runs every iteration (no early exit from the
 // pair loop) and the Blender also provides
 //   void end_item(int k);                            warp-converged, after item k
 //   void end_batch(uint32_t b0, int cnt);            block-converged, after a batch
 // The arithmetic, and so every blend decision, is the same either way.
 template <bool CONVERGENT, class Blender>
-__device__ __forceinline__ void traverse_tile(TileSmem& s, const uint2 range, const uint32_t* __restrict__ keys,
+__device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>& sm, const uint2 range, const uint32_t* __restrict__ keys,
                                               const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
-                                              const FrameConst& fc, int tile_x, int tile_y, float x, float y,
-                                              Blender& bl, unsigned long long& neval, uint32_t& nmis) {
-  const float cxm = fc.cx - (float)(tile_x * kTile), cym = fc.cy - (float)(tile_y * kTile);
+                                              const uint4* __restrict__ aux, const FrameConst& fc, int tile_x,
+                                              int tile_y, float x, float y, Blender& bl,
+                                              unsigned long long& neval, uint32_t& nmis) {
+  const int ox = tile_x * kTile, oy = tile_y * kTile;
+  const float cxm = fc.cx - (float)ox, cym = fc.cy - (float)oy;
+  const uint32_t wbit = 1u << (threadIdx.x >> 5);
   const float kInf = __int_as_float(0x7f800000);
-  SmemQueue q;
-  q.s = &s;
+  StageSmem& s = sm.st;
+  SmemQueue<typename Blender::Queue> q;
+  q.q = &sm.q;
   q.tid = threadIdx.x;
-  q.head = 0;
   q.n = 0;
+  q.order = 0ull;
+  q.used = 0u;
+  q.ft = 0.0f;
   for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
     if (__syncthreads_count(bl.done) == kTilePixels) break;
     const uint32_t j = b0 + threadIdx.x;
     if (j < range.y) {
       const float Lnext = j + 1 < range.y ? decode_depth(keys[j + 1], fc) : kInf;
-      stage_one(s, threadIdx.x, rec, vals[j], Lnext, fc, cxm, cym);
+      const uint32_t gid = vals[j];
+      const uint4 ax = __ldg(aux + gid);
+      stage_one(s, threadIdx.x, rec, gid, make_uint2(ax.x, ax.y), Lnext, fc, cxm, cym, ox, oy);
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kTilePixels, range.y - b0);
     if (CONVERGENT || !bl.done) {
-      if (!bl.done) neval += (unsigned long long)cnt;
       for (int k = 0; k < cnt; ++k) {
+        const float4 bq = s.b[k];
+        if (!(__float_as_uint(bq.w) & wbit)) continue;   // warp-uniform
         if (!bl.done) {
-          const float4 a = s.a[k], bq = s.b[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
+          ++neval;
+          const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
           const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
           const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
           const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
@@ -182,40 +260,30 @@ __device__ __forceinline__ void traverse_tile(TileSmem& s, const uint2 range, co
             const float raw = a.w * __expf(-0.5f * rho2);
             const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
             if (raw >= kAlphaMin && ts >= fc.znear) {
-              const float Lnext = bq.w;
+              const float Lnext = s.L[k];
               const float ca = fminf(raw, kAlphaMax);
-              const uint32_t cg = vals[b0 + k];
               const EvalState ev{k, n0, n1, n2, d0, d1, d2, inv, rho2};
               // 1. queued entries in front of the new one that nothing later can precede
-              while (q.n > 0 && !bl.done) {
-                const float ft = q.front_t();
-                if (!(ft <= ts && ft < Lnext)) break;
-                bl.blend(q.front_a(), q.front_g());
-                q.pop();
-              }
+              while (q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext) q.release(bl);
               if (!bl.done) {
                 if (ts < Lnext) {
                   // 2. the new contributor, then the rest below L_next
-                  bl.blend_new(ca, cg, ev);
-                  while (q.n > 0 && !bl.done && q.front_t() < Lnext) {
-                    bl.blend(q.front_a(), q.front_g());
-                    q.pop();
-                  }
+                  bl.blend_new(ca, ev);
+                  while (q.n > 0 && !bl.done && q.ft < Lnext) q.release(bl);
                 } else {
                   // 3. queue it; when full, release the nearer of the front and
                   // the new entry early (a potential misorder)
                   bool insert = true;
                   if (q.n == kQueue) {
                     ++nmis;
-                    if (ts < q.front_t()) {
-                      bl.blend_new(ca, cg, ev);
+                    if (ts < q.ft) {
+                      bl.blend_new(ca, ev);
                       insert = false;
                     } else {
-                      bl.blend(q.front_a(), q.front_g());
-                      q.pop();
+                      q.release(bl);
                     }
                   }
-                  if (insert && !bl.done) q.insert(ts, ca, cg);
+                  if (insert && !bl.done) q.insert(ts, ca, bl.payload(k));
                 }
               }
             }
@@ -231,10 +299,7 @@ __device__ __forceinline__ void traverse_tile(TileSmem& s, const uint2 range, co
     if constexpr (CONVERGENT) bl.end_batch(b0, cnt);
     __syncthreads();
   }
-  while (q.n > 0 && !bl.done) {
-    bl.blend(q.front_a(), q.front_g());
-    q.pop();
-  }
+  while (q.n > 0 && !bl.done) q.release(bl);
 }
 
 }  // namespace aaag

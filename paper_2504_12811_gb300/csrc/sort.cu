@@ -28,6 +28,7 @@ constexpr unsigned long long kFlagAggregate = 1ull << 30;
 constexpr unsigned long long kFlagPrefix = 2ull << 30;
 constexpr unsigned long long kCountMask = (1ull << 30) - 1ull;
 constexpr long long kWaitCycles = 2000000000ll;   // ~1 s at 2 GHz
+constexpr int kLookWindow = 8;                    // look-back words loaded per round trip
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -150,26 +151,44 @@ sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
     const uint32_t local_start = block_exclusive_scan_256(count, s_tmp);
     s_digit_start[tid] = local_start;
 
-    // ---- decoupled look-back for digit tid
+    // ---- decoupled look-back for digit tid, kLookWindow predecessors per
+    // round trip: the words of tiles t, t-1, ... are loaded together and
+    // consumed nearest first until an inclusive prefix, or a word not yet
+    // published (then the window is reloaded from there)
     uint32_t prefix = 0;
     if (tile > 0) {
-      int64_t t = tile - 1;
+      int64_t t = tile - 1;   // nearest predecessor not yet consumed
       const long long t0 = clock64();
       bool timed_out = false;
-      while (t >= 0) {
-        unsigned long long w = lb[t * kRadix + tid];
-        while ((w & 0xffffffff00000000ull) != tag || (w & (3ull << 30)) == 0) {
+      for (;;) {
+        unsigned long long w[kLookWindow];
+#pragma unroll
+        for (int j = 0; j < kLookWindow; ++j)
+          w[j] = t - j >= 0 ? lb[(t - j) * kRadix + tid] : (tag | kFlagPrefix);   // tile 0 ends it first
+        int used = 0;
+        bool stop = false, stall = false;
+#pragma unroll
+        for (int j = 0; j < kLookWindow; ++j) {
+          if (!stop && !stall) {
+            const unsigned long long x = w[j];
+            if ((x & 0xffffffff00000000ull) != tag || (x & (3ull << 30)) == 0) {
+              stall = true;
+            } else {
+              prefix += (uint32_t)(x & kCountMask);
+              ++used;
+              stop = (x & kFlagPrefix) != 0;
+            }
+          }
+        }
+        if (stop) break;
+        t -= used;
+        if (used == 0) {
           if (clock64() - t0 > kWaitCycles) {
             timed_out = true;
             break;
           }
           __nanosleep(20);
-          w = lb[t * kRadix + tid];
         }
-        if (timed_out) break;
-        prefix += (uint32_t)(w & kCountMask);
-        if (w & kFlagPrefix) break;
-        --t;
       }
       if (timed_out) atomicExch(timeout_flag, 1ull);
       lb[tile * kRadix + tid] = tag | kFlagPrefix | (unsigned long long)(prefix + count);

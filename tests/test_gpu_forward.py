@@ -30,11 +30,19 @@ def gpu_records(ws, n):
 
 
 def rect_of(aux):
-    tx0 = aux[:, 0] & 0xFFFF
-    ty0 = aux[:, 0] >> 16
-    tx1 = aux[:, 1] & 0xFFFF
-    ty1 = aux[:, 1] >> 16
-    return tx0.astype(np.int64), ty0.astype(np.int64), tx1.astype(np.int64), ty1.astype(np.int64)
+    """Inclusive pixel-centre ranges (x0, y0, x1, y1) of the aux words."""
+    x0 = aux[:, 0] & 0xFFFF
+    y0 = aux[:, 0] >> 16
+    x1 = aux[:, 1] & 0xFFFF
+    y1 = aux[:, 1] >> 16
+    return x0.astype(np.int64), y0.astype(np.int64), x1.astype(np.int64), y1.astype(np.int64)
+
+
+def pixel_centre_range(p1, p2, size):
+    """Pixels i whose centre i + 1/2 lies in [p1, p2], clamped to the image."""
+    lo = np.maximum(np.ceil(p1 - 0.5), 0)
+    hi = np.minimum(np.floor(p2 - 0.5), size - 1)
+    return lo.astype(np.int64), hi.astype(np.int64)
 
 
 def contributing_tiles(prep, cam):
@@ -55,6 +63,28 @@ def contributing_tiles(prep, cam):
     return need
 
 
+def contributing_extent(prep, cam):
+    """Per Gaussian, the bounding box (x0, y0, x1, y1) of the pixels it
+    contributes to (x0 > x1 when none), from the oracle."""
+    W, H = cam.width, cam.height
+    n = prep["alive"].shape[0]
+    x0 = np.full(n, 1 << 30, np.int64)
+    y0 = np.full(n, 1 << 30, np.int64)
+    x1 = np.full(n, -1, np.int64)
+    y1 = np.full(n, -1, np.int64)
+    py, px = np.mgrid[0:H, 0:W]
+    px, py = px.ravel(), py.ravel()
+    for i in range(0, px.size, 1024):
+        rho2, ts = O.ray_maximum(prep, px[i:i + 1024], py[i:i + 1024])
+        _, contrib, _ = O.pixel_alphas(prep, rho2, ts)
+        p_idx, g_idx = np.nonzero(contrib.numpy())
+        np.minimum.at(x0, g_idx, px[i + p_idx])
+        np.maximum.at(x1, g_idx, px[i + p_idx])
+        np.minimum.at(y0, g_idx, py[i + p_idx])
+        np.maximum.at(y1, g_idx, py[i + p_idx])
+    return x0, y0, x1, y1
+
+
 CAMS = [("small", 0), ("small", 1), ("zoomout", 0), ("near", 0)]
 
 
@@ -64,8 +94,8 @@ def test_preprocess_matches_oracle(wl, ci):
     cam = cams[ci]
     ws, _, _, _ = run_frame(scene, cam, stages=("pre",))
     rec, aux, _ = gpu_records(ws, scene.n)
-    tx0, ty0, tx1, ty1 = rect_of(aux)
-    vis = tx0 <= tx1
+    x0, y0, x1, y1 = rect_of(aux)
+    vis = x0 <= x1
     prep = O.prepare(scene, cam)
     alive = prep["alive"].numpy()
     uu = (prep["u_cam"] ** 2).sum(-1).numpy()
@@ -85,13 +115,19 @@ def test_preprocess_matches_oracle(wl, ci):
     assert np.max(np.abs(got - T) / scale) < 2e-5
     np.testing.assert_allclose(rec[vis, 15], oh[vis], rtol=2e-5)
     np.testing.assert_allclose(rec[vis, 12:15], prep["rgb"].numpy()[vis], atol=2e-5)
-    # GPU tile rectangle contains the oracle's bounds rectangle
+    # GPU pixel ranges contain the pixel centres inside the oracle's bounds
     b = O.view_space_bounds(prep)
-    ov = b["valid"].numpy() & vis
-    assert np.all(tx0[ov] <= b["x"]["t1"].numpy()[ov])
-    assert np.all(tx1[ov] >= b["x"]["t2"].numpy()[ov])
-    assert np.all(ty0[ov] <= b["y"]["t1"].numpy()[ov])
-    assert np.all(ty1[ov] >= b["y"]["t2"].numpy()[ov])
+    ox0, ox1 = pixel_centre_range(b["x"]["p1"].numpy(), b["x"]["p2"].numpy(), cam.width)
+    oy0, oy1 = pixel_centre_range(b["y"]["p1"].numpy(), b["y"]["p2"].numpy(), cam.height)
+    ov = b["valid"].numpy() & (ox0 <= ox1) & (oy0 <= oy1) & vis
+    assert ov.sum() > 0
+    assert np.all(x0[ov] <= ox0[ov]) and np.all(x1[ov] >= ox1[ov])
+    assert np.all(y0[ov] <= oy0[ov]) and np.all(y1[ov] >= oy1[ov])
+    # and the pixels that see a Gaussian lie inside its GPU ranges
+    cx0, cy0, cx1, cy1 = contributing_extent(prep, cam)
+    seen = (cx0 <= cx1) & ~edge
+    assert np.all(x0[seen] <= cx0[seen]) and np.all(x1[seen] >= cx1[seen])
+    assert np.all(y0[seen] <= cy0[seen]) and np.all(y1[seen] >= cy1[seen])
     st = stats(ws)
     assert st["n_visible"] == int(vis.sum())
 
