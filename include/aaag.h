@@ -308,7 +308,7 @@ aaag_status aaag_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
  * passes only these two device arrays.  Every other buffer (ping-pong copies,
  * histograms, look-back words) lives in one fixed device array inside the
  * library, sized for aaag_radix_sort_static_capacity() = 2^20 keys (about
- * 8.5 MB, held by every GPU that loads the library until the process exits).
+ * 9 MB, held by every GPU that loads the library until the process exits).
  * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
  * The first call on a device resolves that array's address (once per
  * device, with the device current), so make the first call before any stream

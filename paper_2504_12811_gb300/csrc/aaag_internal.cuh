@@ -16,7 +16,16 @@ constexpr float kTStop = 1e-4f;
 constexpr int kMaxShDegree = 3;
 constexpr int kSortItems = 16;            // keys per thread in a sort pass
 constexpr int kSortThreads = 256;
-constexpr int kSortTileKeys = kSortItems * kSortThreads;   // 4096
+constexpr int kSortTileKeys = kSortItems * kSortThreads;   // 4096: the largest sort tile
+// Sorts of at least kSortWideKeys keys use 16 keys per thread; smaller ones 8
+// (at least half of it) or 4, so that small sorts still spread over every SM.
+constexpr int64_t kSortWideKeys = 1 << 20;
+// Most look-back tiles that a sort of up to n keys uses.
+__host__ __device__ constexpr int64_t sort_max_tiles(int64_t n) {
+  return ((n < kSortWideKeys / 2 ? n : kSortWideKeys / 2) + 1023) / 1024 > (n + 4095) / 4096
+             ? ((n < kSortWideKeys / 2 ? n : kSortWideKeys / 2) + 1023) / 1024
+             : (n + 4095) / 4096;
+}
 constexpr int kMaxTileBits = 16;          // at most 65536 tiles per image
 
 // Frame constants, prepared on the host in double precision and rounded once.
@@ -67,7 +76,9 @@ enum StatSlot : int {
   kStatMisorders = 5,
   kStatOverflow = 6,
   kStatTimeout = 7,
-  kStatSortEpoch = 8,
+  kStatCandidates = 8,     // uint32: Gaussians that passed the early preprocessing test
+  kStatFrameReset = 9,     // slots below this one are cleared at the start of every frame
+  kStatSortEpoch = 13,
   kStatChunks = 9,         // chunks of 32 candidate tiles (K2 work items)
   kStatReplayMismatch = 10,// pixels whose backward replay blended a different count
   kStatBatchCounter = 11,  // uint32 work-item counter of the batched render
@@ -91,6 +102,7 @@ struct aaag_workspace {
   char* base;
   aaag::Record* records;
   uint4* aux;
+  uint32_t* candidates;          // [n] Gaussians that passed the early preprocessing test
   uint32_t* counts;              // [n] chunks of 32 candidate tiles per Gaussian
   uint32_t* offsets;             // [n] exclusive prefix of counts
   int64_t chunk_capacity;

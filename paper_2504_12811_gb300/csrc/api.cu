@@ -35,7 +35,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t records, aux, counts, offsets, partials, owner, mask, pofs, keys0, keys1, vals0, vals1, hist, counters,
+  size_t records, aux, cand, counts, offsets, partials, owner, mask, pofs, keys0, keys1, vals0, vals1, hist, counters,
       lookback, ranges, final_T, n_blended, stats, grad, fc, total;
 };
 
@@ -55,10 +55,11 @@ Layout layout_of(int64_t n, int w, int h, int64_t cap) {
   };
   const int64_t ccap = chunk_capacity_of(n, cap);
   const int64_t nsb = (std::max(n, ccap) + 4095) / 4096 + 1;
-  const int64_t nst = (cap + kSortTileKeys - 1) / kSortTileKeys + 1;
+  const int64_t nst = sort_max_tiles(cap) + 1;
   const size_t ntiles = (size_t)tiles_of(w) * tiles_of(h);
   L.records = take((size_t)n * sizeof(Record));
   L.aux = take((size_t)n * 16);
+  L.cand = take((size_t)n * 4);
   L.counts = take((size_t)n * 4);
   L.offsets = take((size_t)n * 4);
   L.partials = take((size_t)nsb * 8);
@@ -256,6 +257,7 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
   w->base = b;
   w->records = reinterpret_cast<Record*>(b + L.records);
   w->aux = reinterpret_cast<uint4*>(b + L.aux);
+  w->candidates = reinterpret_cast<uint32_t*>(b + L.cand);
   w->counts = reinterpret_cast<uint32_t*>(b + L.counts);
   w->offsets = reinterpret_cast<uint32_t*>(b + L.offsets);
   w->scan_partials = reinterpret_cast<unsigned long long*>(b + L.partials);
@@ -277,7 +279,7 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
   w->grad_acc = reinterpret_cast<float4*>(b + L.grad);
   w->fc_dev = reinterpret_cast<FrameConst*>(b + L.fc);
   w->n_scan_blocks = (n + 4095) / 4096;
-  w->n_sort_tiles = (pair_capacity + kSortTileKeys - 1) / kSortTileKeys;
+  w->n_sort_tiles = sort_max_tiles(pair_capacity);
   // the look-back epoch lives in the stats block and must start defined; the
   // look-back words are cleared once so that no stale word can match an epoch
   if (cudaMemset(w->stats, 0, kStatCount * 8) != cudaSuccess ||
@@ -363,7 +365,7 @@ aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, 
   e = check_launch("set_frame");
   if (e != AAAG_OK) return e;
   // reset per-frame statistics (keep the sort epoch)
-  if (cudaMemsetAsync(ws->stats, 0, kStatSortEpoch * 8, stream) != cudaSuccess)
+  if (cudaMemsetAsync(ws->stats, 0, kStatFrameReset * 8, stream) != cudaSuccess)
     return check_launch("preprocess memset");
   return launch_preprocess(scene_dev(scene), ws, stream);
 }

@@ -6,6 +6,8 @@
 // hundred FP32 operations per Gaussian.
 #include <cmath>
 
+#include <algorithm>
+
 #include "aaag_internal.cuh"
 #include "geometry.cuh"
 
@@ -116,203 +118,284 @@ __device__ __forceinline__ bool pixel_range(float p1, float p2, int size, int& i
   return i0 <= i1;
 }
 
-__global__ void __launch_bounds__(256)
-preprocess_kernel(SceneDev s, const FrameConst* __restrict__ fcp, Record* __restrict__ rec, uint4* __restrict__ aux,
-                  uint32_t* __restrict__ chunks, unsigned long long* __restrict__ stats) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool visible = false;
-  if (i < s.n) {
-    const FrameConst fc = *fcp;
-    const float mx = s.means[3 * i + 0], my = s.means[3 * i + 1], mz = s.means[3 * i + 2];
-    const float lx = s.log_scales[3 * i + 0], ly = s.log_scales[3 * i + 1],
-                lz = s.log_scales[3 * i + 2];
-    const float4 q4 = reinterpret_cast<const float4*>(s.quats)[i];
-    const float logit = s.opacity_logits[i];
-    const float vtrain = s.vhat_train[i];
+// Activations, view-space mean and filtered variances of Gaussian i (the part
+// every Gaussian needs before the early test).
+struct Basic {
+  float mx, my, mz;      // mean (world)
+  float vx, vy, vz;      // mean (view)
+  float s2x, s2y, s2z;   // variances s^2
+  float hx, hy, hz;      // filtered variances s^2 + k / v'^2 (Eq. 6, 13)
+  float opac;
+};
 
-    // view-space mean
-    const float vx = fc.Rv[0] * mx + fc.Rv[1] * my + fc.Rv[2] * mz + fc.tv[0];
-    const float vy = fc.Rv[3] * mx + fc.Rv[4] * my + fc.Rv[5] * mz + fc.tv[1];
-    const float vz = fc.Rv[6] * mx + fc.Rv[7] * my + fc.Rv[8] * mz + fc.tv[2];
+__device__ __forceinline__ Basic load_basic(const SceneDev& s, const FrameConst& fc, int64_t i) {
+  Basic b;
+  b.mx = s.means[3 * i + 0];
+  b.my = s.means[3 * i + 1];
+  b.mz = s.means[3 * i + 2];
+  const float lx = s.log_scales[3 * i + 0], ly = s.log_scales[3 * i + 1], lz = s.log_scales[3 * i + 2];
+  const float logit = s.opacity_logits[i];
+  const float vtrain = s.vhat_train[i];
+  // view-space mean
+  b.vx = fc.Rv[0] * b.mx + fc.Rv[1] * b.my + fc.Rv[2] * b.mz + fc.tv[0];
+  b.vy = fc.Rv[3] * b.mx + fc.Rv[4] * b.my + fc.Rv[5] * b.mz + fc.tv[1];
+  b.vz = fc.Rv[6] * b.mx + fc.Rv[7] * b.my + fc.Rv[8] * b.mz + fc.tv[2];
+  // activations (Sec. 3.1)
+  const float sx = expf(lx), sy = expf(ly), sz = expf(lz);
+  b.opac = 1.0f / (1.0f + expf(-logit));
+  // adaptive filter (Eq. 6, 13)
+  float kv = 0.0f;
+  if (!(fc.flags & AAAG_FLAG_NO_FILTER)) {
+    const float vhat = fc.fx / fmaxf(b.vz, fc.znear);
+    const float veff = fminf(vtrain, vhat);
+    kv = fc.k / (veff * veff);
+  }
+  b.s2x = sx * sx;
+  b.s2y = sy * sy;
+  b.s2z = sz * sz;
+  b.hx = b.s2x + kv;
+  b.hy = b.s2y + kv;
+  b.hz = b.s2z + kv;
+  return b;
+}
 
-    // activations (Sec. 3.1)
-    const float sx = expf(lx), sy = expf(ly), sz = expf(lz);
-    float qn = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
-    const float qi = qn > 0.0f ? rsqrtf(qn) : 0.0f;
-    const float w = qn > 0.0f ? q4.x * qi : 1.0f;
-    const float qx = q4.y * qi, qy = q4.z * qi, qz = q4.w * qi;
-    float R[9];
-    R[0] = 1.0f - 2.0f * (qy * qy + qz * qz);
-    R[1] = 2.0f * (qx * qy - w * qz);
-    R[2] = 2.0f * (qx * qz + w * qy);
-    R[3] = 2.0f * (qx * qy + w * qz);
-    R[4] = 1.0f - 2.0f * (qx * qx + qz * qz);
-    R[5] = 2.0f * (qy * qz - w * qx);
-    R[6] = 2.0f * (qx * qz - w * qy);
-    R[7] = 2.0f * (qy * qz + w * qx);
-    R[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
-    const float opac = 1.0f / (1.0f + expf(-logit));
-
-    // adaptive filter (Eq. 6, 12, 13)
-    float kv = 0.0f;
-    if (!(fc.flags & AAAG_FLAG_NO_FILTER)) {
-      const float vhat = fc.fx / fmaxf(vz, fc.znear);
-      const float veff = fminf(vtrain, vhat);
-      kv = fc.k / (veff * veff);
-    }
-    const float s2x = sx * sx, s2y = sy * sy, s2z = sz * sz;
-    const float hx = s2x + kv, hy = s2y + kv, hz = s2z + kv;
-    // Conservative early reject.  The tau-ellipsoid lies inside the sphere
-    // of radius sqrt(tau_max * max_i s_hat_i^2) around the mean, where
-    // tau_max = 2 ln(255 o) >= tau because the amplitude factor of Eq. 12 is
-    // at most 1.  A sphere wholly outside one side plane of the image frustum
-    // or in front of z_near holds no visible point, and the remaining work is
-    // skipped (most Gaussians of a large scene are outside the view).
-    const float tau_max = 2.0f * logf(fmaxf(opac * 255.0f, 1.0f));
-    const float rad = fmaf(sqrtf(inflate_tau(tau_max) * fmaxf(hx, fmaxf(hy, hz))), 1.001f, 1e-6f);
-    bool near_view = vz + rad >= fc.znear && opac > kAlphaMin;
+// Conservative early test.  The tau-ellipsoid lies inside the sphere of
+// radius sqrt(tau_max * max_i s_hat_i^2) around the mean, where tau_max =
+// 2 ln(255 o) >= tau because the amplitude factor of Eq. 12 is at most 1.  A
+// sphere wholly outside one side plane of the image frustum or in front of
+// z_near holds no visible point.
+__device__ __forceinline__ bool may_be_visible(const Basic& b, const FrameConst& fc) {
+  const float tau_max = 2.0f * logf(fmaxf(b.opac * 255.0f, 1.0f));
+  const float rad = fmaf(sqrtf(inflate_tau(tau_max) * fmaxf(b.hx, fmaxf(b.hy, b.hz))), 1.001f, 1e-6f);
+  bool near_view = b.vz + rad >= fc.znear && b.opac > kAlphaMin;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      near_view &= fmaf(fc.side[j][0], vx, fmaf(fc.side[j][1], vy, fc.side[j][2] * vz)) >= -rad;
-    if (near_view) {
-      // d = unit vector camera -> mean; d' = R^T d
-      const float dx0 = mx - fc.o[0], dy0 = my - fc.o[1], dz0 = mz - fc.o[2];
-      const float dist = sqrtf(dx0 * dx0 + dy0 * dy0 + dz0 * dz0);
-      const float idist = 1.0f / dist;
-      const float ddx = dx0 * idist, ddy = dy0 * idist, ddz = dz0 * idist;
-      const float p0 = R[0] * ddx + R[3] * ddy + R[6] * ddz;
-      const float p1 = R[1] * ddx + R[4] * ddy + R[7] * ddz;
-      const float p2 = R[2] * ddx + R[5] * ddy + R[8] * ddz;
-      // Eq. 12 divided through by s_hat_1 s_hat_2 s_hat_3: a weighted mean of
-      // r_j r_k with weights d'_i^2 / s_hat_i, r_j = s_j^2 / s_hat_j
-      const float w0 = p0 * p0 / hx, w1 = p1 * p1 / hy, w2 = p2 * p2 / hz;
-      const float r0 = s2x / hx, r1 = s2y / hy, r2 = s2z / hz;
-      const float phi2 = (w0 * r1 * r2 + w1 * r0 * r2 + w2 * r0 * r1) / (w0 + w1 + w2);
-      const float o_hat = opac * sqrtf(phi2);
+  for (int j = 0; j < 4; ++j)
+    near_view &= fmaf(fc.side[j][0], b.vx, fmaf(fc.side[j][1], b.vy, fc.side[j][2] * b.vz)) >= -rad;
+  return near_view;
+}
 
-      if (o_hat > kAlphaMin) {
-        const float tau = 2.0f * logf(o_hat * 255.0f);
-        const float spx = sqrtf(hx), spy = sqrtf(hy), spz = sqrtf(hz);
-        // camera origin in normalised Gaussian space: S'^-1 R^T (o - mu)
-        const float ux = -dist * p0 / spx, uy = -dist * p1 / spy, uz = -dist * p2 / spz;
-        const bool inside = ux * ux + uy * uy + uz * uz < tau;
-        // A = Rv R S': rows are the view axes expressed in the Gaussian frame
-        float A[9];
-  #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const float a0 = fc.Rv[3 * r + 0] * R[0] + fc.Rv[3 * r + 1] * R[3] + fc.Rv[3 * r + 2] * R[6];
-          const float a1 = fc.Rv[3 * r + 0] * R[1] + fc.Rv[3 * r + 1] * R[4] + fc.Rv[3 * r + 2] * R[7];
-          const float a2 = fc.Rv[3 * r + 0] * R[2] + fc.Rv[3 * r + 1] * R[5] + fc.Rv[3 * r + 2] * R[8];
-          A[3 * r + 0] = a0 * spx;
-          A[3 * r + 1] = a1 * spy;
-          A[3 * r + 2] = a2 * spz;
+// Full preprocessing of a Gaussian that passed the early test.  Writes its
+// record, aux word and chunk count and returns true when it is visible;
+// writes nothing otherwise.
+__device__ __forceinline__ bool preprocess_one(const SceneDev& s, const FrameConst& fc, int64_t i,
+                                               Record* __restrict__ rec, uint4* __restrict__ aux,
+                                               uint32_t* __restrict__ chunks) {
+  const Basic bb = load_basic(s, fc, i);
+  const float mx = bb.mx, my = bb.my, mz = bb.mz, vx = bb.vx, vy = bb.vy, vz = bb.vz;
+  const float s2x = bb.s2x, s2y = bb.s2y, s2z = bb.s2z, hx = bb.hx, hy = bb.hy, hz = bb.hz;
+  const float opac = bb.opac;
+  const float4 q4 = reinterpret_cast<const float4*>(s.quats)[i];
+  float qn = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+  const float qi = qn > 0.0f ? rsqrtf(qn) : 0.0f;
+  const float w = qn > 0.0f ? q4.x * qi : 1.0f;
+  const float qx = q4.y * qi, qy = q4.z * qi, qz = q4.w * qi;
+  float R[9];
+  R[0] = 1.0f - 2.0f * (qy * qy + qz * qz);
+  R[1] = 2.0f * (qx * qy - w * qz);
+  R[2] = 2.0f * (qx * qz + w * qy);
+  R[3] = 2.0f * (qx * qy + w * qz);
+  R[4] = 1.0f - 2.0f * (qx * qx + qz * qz);
+  R[5] = 2.0f * (qy * qz - w * qx);
+  R[6] = 2.0f * (qx * qz - w * qy);
+  R[7] = 2.0f * (qy * qz + w * qx);
+  R[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
+  bool visible = false;
+  // d = unit vector camera -> mean; d' = R^T d
+  const float dx0 = mx - fc.o[0], dy0 = my - fc.o[1], dz0 = mz - fc.o[2];
+  const float dist = sqrtf(dx0 * dx0 + dy0 * dy0 + dz0 * dz0);
+  const float idist = 1.0f / dist;
+  const float ddx = dx0 * idist, ddy = dy0 * idist, ddz = dz0 * idist;
+  const float p0 = R[0] * ddx + R[3] * ddy + R[6] * ddz;
+  const float p1 = R[1] * ddx + R[4] * ddy + R[7] * ddz;
+  const float p2 = R[2] * ddx + R[5] * ddy + R[8] * ddz;
+  // Eq. 12 divided through by s_hat_1 s_hat_2 s_hat_3: a weighted mean of
+  // r_j r_k with weights d'_i^2 / s_hat_i, r_j = s_j^2 / s_hat_j
+  const float w0 = p0 * p0 / hx, w1 = p1 * p1 / hy, w2 = p2 * p2 / hz;
+  const float r0 = s2x / hx, r1 = s2y / hy, r2 = s2z / hz;
+  const float phi2 = (w0 * r1 * r2 + w1 * r0 * r2 + w2 * r0 * r1) / (w0 + w1 + w2);
+  const float o_hat = opac * sqrtf(phi2);
+
+  if (o_hat > kAlphaMin) {
+    const float tau = 2.0f * logf(o_hat * 255.0f);
+    const float spx = sqrtf(hx), spy = sqrtf(hy), spz = sqrtf(hz);
+    // camera origin in normalised Gaussian space: S'^-1 R^T (o - mu)
+    const float ux = -dist * p0 / spx, uy = -dist * p1 / spy, uz = -dist * p2 / spz;
+    const bool inside = ux * ux + uy * uy + uz * uz < tau;
+    // A = Rv R S': rows are the view axes expressed in the Gaussian frame
+    float A[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float a0 = fc.Rv[3 * r + 0] * R[0] + fc.Rv[3 * r + 1] * R[3] + fc.Rv[3 * r + 2] * R[6];
+      const float a1 = fc.Rv[3 * r + 0] * R[1] + fc.Rv[3 * r + 1] * R[4] + fc.Rv[3 * r + 2] * R[7];
+      const float a2 = fc.Rv[3 * r + 0] * R[2] + fc.Rv[3 * r + 1] * R[5] + fc.Rv[3 * r + 2] * R[8];
+      A[3 * r + 0] = a0 * spx;
+      A[3 * r + 1] = a1 * spy;
+      A[3 * r + 2] = a2 * spz;
+    }
+    const float3 A1 = f3(A[0], A[1], A[2]), A2 = f3(A[3], A[4], A[5]), A3 = f3(A[6], A[7], A[8]);
+    const float tau_c = inflate_tau(tau);
+    const float zext = sqrtf(tau_c * dot3(A3, A3));
+    const float z_lo = vz - zext, z_hi = vz + zext;
+    int ix0 = 1, ix1 = 0, iy0 = 1, iy1 = 0;   // pixel-centre ranges
+    bool ok = !inside && z_hi >= fc.znear;
+    if (ok) {
+      float px1, px2, py1, py2;
+      ok = axis_bounds(A1, A3, vx, vz, tau_c, fc.fx, fc.cx, fc.eps, px1, px2) &&
+           axis_bounds(A2, A3, vy, vz, tau_c, fc.fy, fc.cy, fc.eps, py1, py2) &&
+           pixel_range(px1, px2, fc.W, ix0, ix1) && pixel_range(py1, py2, fc.H, iy0, iy1);
+    }
+    const float4 t1 = make_float4(A[0], A[1], A[2], vx);
+    const float4 t2 = make_float4(A[3], A[4], A[5], vy);
+    const float4 t3 = make_float4(A[6], A[7], A[8], vz);
+    if (ok) {
+      // whole-image frustum cull (Sec. 3.4, last paragraph)
+      const float W = (float)fc.W, H = (float)fc.H;
+      ok = (z_lo < fc.znear)
+               ? frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, 0.f, W, 0.f, H, tau_c)
+               : frustum_hit<false>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, 0.f, W, 0.f, H, tau_c);
+    }
+    if (ok) {
+      visible = true;
+      // colour (view-dependent, real SH up to degree 3)
+      const int K = (s.sh_degree + 1) * (s.sh_degree + 1);
+      float Y[16];
+      sh_basis(ddx, ddy, ddz, s.sh_degree, Y);
+      float cr = 0.5f, cg = 0.5f, cb = 0.5f;
+      const float* shp = s.sh + (size_t)i * K * 3;
+      if (K == 16) {
+        const float4* s4 = reinterpret_cast<const float4*>(shp);
+        float c[48];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+          const float4 v = s4[j];
+          c[4 * j + 0] = v.x; c[4 * j + 1] = v.y; c[4 * j + 2] = v.z; c[4 * j + 3] = v.w;
         }
-        const float3 A1 = f3(A[0], A[1], A[2]), A2 = f3(A[3], A[4], A[5]), A3 = f3(A[6], A[7], A[8]);
-        const float tau_c = inflate_tau(tau);
-        const float zext = sqrtf(tau_c * dot3(A3, A3));
-        const float z_lo = vz - zext, z_hi = vz + zext;
-        int ix0 = 1, ix1 = 0, iy0 = 1, iy1 = 0;   // pixel-centre ranges
-        bool ok = !inside && z_hi >= fc.znear;
-        if (ok) {
-          float px1, px2, py1, py2;
-          ok = axis_bounds(A1, A3, vx, vz, tau_c, fc.fx, fc.cx, fc.eps, px1, px2) &&
-               axis_bounds(A2, A3, vy, vz, tau_c, fc.fy, fc.cy, fc.eps, py1, py2) &&
-               pixel_range(px1, px2, fc.W, ix0, ix1) && pixel_range(py1, py2, fc.H, iy0, iy1);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          cr += Y[j] * c[3 * j + 0];
+          cg += Y[j] * c[3 * j + 1];
+          cb += Y[j] * c[3 * j + 2];
         }
-        const float4 t1 = make_float4(A[0], A[1], A[2], vx);
-        const float4 t2 = make_float4(A[3], A[4], A[5], vy);
-        const float4 t3 = make_float4(A[6], A[7], A[8], vz);
-        if (ok) {
-          // whole-image frustum cull (Sec. 3.4, last paragraph)
-          const float W = (float)fc.W, H = (float)fc.H;
-          ok = (z_lo < fc.znear)
-                   ? frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, 0.f, W, 0.f, H, tau_c)
-                   : frustum_hit<false>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, 0.f, W, 0.f, H, tau_c);
-        }
-        if (ok) {
-          visible = true;
-          // colour (view-dependent, real SH up to degree 3)
-          const int K = (s.sh_degree + 1) * (s.sh_degree + 1);
-          float Y[16];
-          sh_basis(ddx, ddy, ddz, s.sh_degree, Y);
-          float cr = 0.5f, cg = 0.5f, cb = 0.5f;
-          const float* shp = s.sh + (size_t)i * K * 3;
-          if (K == 16) {
-            const float4* s4 = reinterpret_cast<const float4*>(shp);
-            float c[48];
-  #pragma unroll
-            for (int j = 0; j < 12; ++j) {
-              const float4 v = s4[j];
-              c[4 * j + 0] = v.x; c[4 * j + 1] = v.y; c[4 * j + 2] = v.z; c[4 * j + 3] = v.w;
-            }
-  #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              cr += Y[j] * c[3 * j + 0];
-              cg += Y[j] * c[3 * j + 1];
-              cb += Y[j] * c[3 * j + 2];
-            }
-          } else {
-            for (int j = 0; j < K; ++j) {
-              cr += Y[j] * shp[3 * j + 0];
-              cg += Y[j] * shp[3 * j + 1];
-              cb += Y[j] * shp[3 * j + 2];
-            }
-          }
-          Record out;
-          out.t1 = t1;
-          out.t2 = t2;
-          out.t3 = t3;
-          out.rgba = make_float4(fmaxf(cr, 0.0f), fmaxf(cg, 0.0f), fmaxf(cb, 0.0f), o_hat);
-          rec[i] = out;
-          // Depth key: a lower bound of the depth t* of the maximum on every
-          // contributing ray.  In normalised Gaussian space the maximum u* of a
-          // ray from the camera c is the foot of the perpendicular from the
-          // origin, so u*.(u* - c) = 0: u* lies on the sphere |u|^2 = u.c, and
-          // contributing means |u*|^2 <= tau.  Hence u*.c_hat is in
-          // [0, tau/|c|] and the part of u* orthogonal to c_hat has length
-          // <= sqrt(tau); the view depth Z = A3.u + mu_z is then at least
-          //   mu_z - sqrt(tau) |A3_perp| + min(0, A3.c_hat) tau / |c|,
-          // with A3_perp the part of A3 orthogonal to c_hat.  This is never
-          // below the front of the tau-ellipsoid (|A3_perp| <= |A3|) and is much
-          // tighter for Gaussians seen head-on.  Quantised max(bound, znear),
-          // rounded down.
-          const float cn = sqrtf(ux * ux + uy * uy + uz * uz);
-          const float3 ch = (1.0f / cn) * f3(ux, uy, uz);
-          const float a3c = dot3(A3, ch);
-          const float3 A3p = A3 - a3c * ch;
-          float t_lo = vz - sqrtf(tau_c * dot3(A3p, A3p)) + fminf(a3c, 0.0f) * tau_c / cn;
-          t_lo -= 1e-5f * fabsf(t_lo) + 1e-6f;
-          const float zk = fmaxf(fmaxf(t_lo, z_lo), fc.znear);
-          uint32_t dk = (__float_as_uint(zk) - fc.znear_bits) >> fc.depth_shift;
-          const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
-          dk = min(dk, dmax);
-          // tau_rho, negated when the front of the ellipsoid reaches znear (the
-          // tile test then truncates the frustum at the near plane)
-          aux[i] = make_uint4((uint32_t)ix0 | ((uint32_t)iy0 << 16), (uint32_t)ix1 | ((uint32_t)iy1 << 16),
-                              __float_as_uint(z_lo < fc.znear ? -tau : tau), dk);
-          const uint32_t ntiles = (uint32_t)((ix1 / kTile) - (ix0 / kTile) + 1) *
-                                  (uint32_t)((iy1 / kTile) - (iy0 / kTile) + 1);
-          chunks[i] = (ntiles + 31u) / 32u;
+      } else {
+        for (int j = 0; j < K; ++j) {
+          cr += Y[j] * shp[3 * j + 0];
+          cg += Y[j] * shp[3 * j + 1];
+          cb += Y[j] * shp[3 * j + 2];
         }
       }
+      Record out;
+      out.t1 = t1;
+      out.t2 = t2;
+      out.t3 = t3;
+      out.rgba = make_float4(fmaxf(cr, 0.0f), fmaxf(cg, 0.0f), fmaxf(cb, 0.0f), o_hat);
+      rec[i] = out;
+      // Depth key: a lower bound of the depth t* of the maximum on every
+      // contributing ray.  In normalised Gaussian space the maximum u* of a
+      // ray from the camera c is the foot of the perpendicular from the
+      // origin, so u*.(u* - c) = 0: u* lies on the sphere |u|^2 = u.c, and
+      // contributing means |u*|^2 <= tau.  Hence u*.c_hat is in
+      // [0, tau/|c|] and the part of u* orthogonal to c_hat has length
+      // <= sqrt(tau); the view depth Z = A3.u + mu_z is then at least
+      //   mu_z - sqrt(tau) |A3_perp| + min(0, A3.c_hat) tau / |c|,
+      // with A3_perp the part of A3 orthogonal to c_hat.  This is never
+      // below the front of the tau-ellipsoid (|A3_perp| <= |A3|) and is much
+      // tighter for Gaussians seen head-on.  Quantised max(bound, znear),
+      // rounded down.
+      const float cn = sqrtf(ux * ux + uy * uy + uz * uz);
+      const float3 ch = (1.0f / cn) * f3(ux, uy, uz);
+      const float a3c = dot3(A3, ch);
+      const float3 A3p = A3 - a3c * ch;
+      float t_lo = vz - sqrtf(tau_c * dot3(A3p, A3p)) + fminf(a3c, 0.0f) * tau_c / cn;
+      t_lo -= 1e-5f * fabsf(t_lo) + 1e-6f;
+      const float zk = fmaxf(fmaxf(t_lo, z_lo), fc.znear);
+      uint32_t dk = (__float_as_uint(zk) - fc.znear_bits) >> fc.depth_shift;
+      const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
+      dk = min(dk, dmax);
+      // tau_rho, negated when the front of the ellipsoid reaches znear (the
+      // tile test then truncates the frustum at the near plane)
+      aux[i] = make_uint4((uint32_t)ix0 | ((uint32_t)iy0 << 16), (uint32_t)ix1 | ((uint32_t)iy1 << 16),
+                          __float_as_uint(z_lo < fc.znear ? -tau : tau), dk);
+      const uint32_t ntiles = (uint32_t)((ix1 / kTile) - (ix0 / kTile) + 1) *
+                              (uint32_t)((iy1 / kTile) - (iy0 / kTile) + 1);
+      chunks[i] = (ntiles + 31u) / 32u;
     }
-    if (!visible) {
+  }
+  return visible;
+}
+
+// Phase 1, one thread per Gaussian: the early test.  Rejected Gaussians get
+// an empty rectangle; the others are appended to the candidate list (in a
+// large scene only a few percent survive, scattered over the warps, so the
+// full work runs in a second kernel on converged warps).
+__global__ void __launch_bounds__(256)
+preprocess_test_kernel(SceneDev s, const FrameConst* __restrict__ fcp, uint4* __restrict__ aux,
+                       uint32_t* __restrict__ chunks, uint32_t* __restrict__ cand,
+                       uint32_t* __restrict__ n_cand) {
+  const FrameConst fc = *fcp;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool pass = false;
+  if (i < s.n) {
+    pass = may_be_visible(load_basic(s, fc, i), fc);
+    if (!pass) {
       aux[i] = make_uint4(1u, 0u, 0u, 0u);   // empty rectangle
       chunks[i] = 0u;
     }
   }
-  const unsigned ball = __ballot_sync(0xffffffffu, visible);
-  if ((threadIdx.x & 31) == 0 && ball) atomicAdd(&stats[kStatVisible], (unsigned long long)__popc(ball));
+  const unsigned ball = __ballot_sync(0xffffffffu, pass);
+  uint32_t at = 0u;
+  if (lane == 0 && ball) at = atomicAdd(n_cand, (uint32_t)__popc(ball));
+  at = __shfl_sync(0xffffffffu, at, 0);
+  if (pass) cand[at + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
 }
+
+// Phase 2: full preprocessing of the candidates (grid-stride over the count
+// left in device memory by phase 1).
+__global__ void __launch_bounds__(256, 3)
+preprocess_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const uint32_t* __restrict__ cand,
+                  const uint32_t* __restrict__ n_cand, Record* __restrict__ rec, uint4* __restrict__ aux,
+                  uint32_t* __restrict__ chunks, unsigned long long* __restrict__ stats) {
+  const FrameConst fc = *fcp;
+  const uint32_t count = *n_cand;
+  uint32_t nvis = 0;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j - threadIdx.x < count; j += gridDim.x * blockDim.x) {
+    bool visible = false;
+    if (j < count) {
+      const int64_t g = cand[j];
+      visible = preprocess_one(s, fc, g, rec, aux, chunks);
+      if (!visible) {
+        aux[g] = make_uint4(1u, 0u, 0u, 0u);
+        chunks[g] = 0u;
+      }
+    }
+    nvis += (uint32_t)__popc(__ballot_sync(0xffffffffu, visible));
+  }
+  if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(&stats[kStatVisible], (unsigned long long)nvis);
+}
+
+int g_pre_blocks = 0;
 
 }  // namespace
 
 aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_t st) {
   if (s.n == 0) return AAAG_OK;
+  if (!g_pre_blocks) {
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, preprocess_kernel, 256, 0);
+    g_pre_blocks = std::max(1, sms) * std::max(1, per_sm);
+  }
   const int threads = 256;
   const int64_t blocks = (s.n + threads - 1) / threads;
-  preprocess_kernel<<<(unsigned)blocks, threads, 0, st>>>(s, ws->fc_dev, ws->records, ws->aux, ws->counts,
-                                                          ws->stats);
+  uint32_t* n_cand = reinterpret_cast<uint32_t*>(ws->stats + kStatCandidates);
+  preprocess_test_kernel<<<(unsigned)blocks, threads, 0, st>>>(s, ws->fc_dev, ws->aux, ws->counts,
+                                                               ws->candidates, n_cand);
+  aaag_status e = check_launch("preprocess_test");
+  if (e != AAAG_OK) return e;
+  const unsigned grid = (unsigned)std::min<int64_t>(blocks, g_pre_blocks);
+  preprocess_kernel<<<grid, threads, 0, st>>>(s, ws->fc_dev, ws->candidates, n_cand, ws->records, ws->aux,
+                                              ws->counts, ws->stats);
   return check_launch("preprocess");
 }
 

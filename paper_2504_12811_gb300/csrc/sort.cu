@@ -78,30 +78,34 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
   return pre + x - v;
 }
 
-__global__ void __launch_bounds__(kSortThreads)
-sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                 const uint32_t* __restrict__ n_dev, int64_t n_max, int pass,
-                 const uint32_t* __restrict__ hist, uint32_t* __restrict__ counter,
-                 unsigned long long* __restrict__ lookback,
-                 const unsigned long long* __restrict__ epoch_dev,
-                 unsigned long long* __restrict__ timeout_flag) {
-  __shared__ uint32_t s_keys[kSortTileKeys];
-  __shared__ uint32_t s_vals[kSortTileKeys];
-  __shared__ uint32_t s_warp[kSortThreads / 32][kRadix];   // per-warp digit counts -> prefixes
-  __shared__ uint32_t s_digit_start[kRadix];               // block-local digit starts
-  __shared__ uint32_t s_global[kRadix];                    // global start of this block's digits
-  __shared__ uint32_t s_tmp[8];
-  __shared__ int s_tile;
+struct SortSmem {
+  uint32_t keys[kSortTileKeys];
+  uint32_t vals[kSortTileKeys];
+  uint32_t warp[kSortThreads / 32][kRadix];   // per-warp digit counts -> prefixes
+  uint32_t digit_start[kRadix];               // block-local digit starts
+  uint32_t global[kRadix];                    // global start of this block's digits
+  uint32_t tmp[8];
+  int tile;
+};
 
+// Tiles of ITEMS keys per thread, taken in order from the pass counter.
+template <int ITEMS>
+__device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __restrict__ keys_in,
+                                                const uint32_t* __restrict__ vals_in,
+                                                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                                                int64_t n, int shift, uint32_t gofs, uint32_t* __restrict__ counter,
+                                                unsigned long long* __restrict__ lookback, unsigned long long tag,
+                                                unsigned long long* __restrict__ timeout_flag) {
+  constexpr int kTileKeys = ITEMS * kSortThreads;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int shift = 8 * pass;
-  const int64_t n = min((int64_t)*n_dev, n_max);
-  const int64_t n_tiles = (n + kSortTileKeys - 1) / kSortTileKeys;
-  const unsigned long long epoch = ((*epoch_dev) * 8ull + (unsigned long long)pass) & 0xffffffffull;
-  const unsigned long long tag = epoch << 32;
-  // global exclusive offset of digit `tid` for this pass
-  const uint32_t gofs = block_exclusive_scan_256(hist[pass * kRadix + tid], s_tmp);
+  const int64_t n_tiles = (n + kTileKeys - 1) / kTileKeys;
+  uint32_t* s_keys = sm.keys;
+  uint32_t* s_vals = sm.vals;
+  uint32_t (*s_warp)[kRadix] = sm.warp;
+  uint32_t* s_digit_start = sm.digit_start;
+  uint32_t* s_global = sm.global;
+  uint32_t* s_tmp = sm.tmp;
+  int& s_tile = sm.tile;
 
   for (;;) {
     if (tid == 0) s_tile = (int)atomicAdd(counter, 1u);
@@ -110,10 +114,10 @@ sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
     if (tile >= n_tiles) break;
 
     // ---- load (warp-striped: coalesced) and rank within each warp
-    uint32_t k[kSortItems], v[kSortItems], r[kSortItems];
-    const int64_t base = tile * kSortTileKeys + (int64_t)warp * (32 * kSortItems);
+    uint32_t k[ITEMS], v[ITEMS], r[ITEMS];
+    const int64_t base = tile * kTileKeys + (int64_t)warp * (32 * ITEMS);
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
       const int64_t idx = base + j * 32 + lane;
       const bool ok = idx < n;
       k[j] = ok ? keys_in[idx] : 0xffffffffu;
@@ -123,7 +127,7 @@ sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
     __syncwarp();
     const unsigned lt = lanemask_lt();
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
       const uint32_t d = (k[j] >> shift) & 0xffu;
       const unsigned peers = __match_any_sync(0xffffffffu, d);
       const uint32_t before = s_warp[warp][d];
@@ -198,15 +202,15 @@ sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
 
     // ---- scatter into shared memory in digit order, then to global memory
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
       const uint32_t d = (k[j] >> shift) & 0xffu;
       const uint32_t pos = s_digit_start[d] + s_warp[warp][d] + r[j];
       s_keys[pos] = k[j];
       s_vals[pos] = v[j];
     }
     __syncthreads();
-    const int64_t valid = min((int64_t)kSortTileKeys, n - tile * kSortTileKeys);
-    for (int q = tid; q < kSortTileKeys; q += kSortThreads) {
+    const int64_t valid = min((int64_t)kTileKeys, n - tile * kTileKeys);
+    for (int q = tid; q < kTileKeys; q += kSortThreads) {
       const uint32_t key = s_keys[q];
       const uint32_t d = (key >> shift) & 0xffu;
       const int64_t g = (int64_t)s_global[d] + (q - (int64_t)s_digit_start[d]);
@@ -219,6 +223,38 @@ sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
     }
     __syncthreads();
   }
+}
+
+// Keys per thread by problem size: small sorts use small tiles so that every
+// SM has work and the look-back chains stay short in time.
+__device__ __forceinline__ int sort_items_for(int64_t n) {
+  return n >= kSortWideKeys ? 16 : (n >= kSortWideKeys / 2 ? 8 : 4);
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                 const uint32_t* __restrict__ n_dev, int64_t n_max, int pass,
+                 const uint32_t* __restrict__ hist, uint32_t* __restrict__ counter,
+                 unsigned long long* __restrict__ lookback,
+                 const unsigned long long* __restrict__ epoch_dev,
+                 unsigned long long* __restrict__ timeout_flag) {
+  __shared__ SortSmem sm;
+  const int64_t n = min((int64_t)*n_dev, n_max);
+  const unsigned long long epoch = ((*epoch_dev) * 8ull + (unsigned long long)pass) & 0xffffffffull;
+  const unsigned long long tag = epoch << 32;
+  // global exclusive offset of digit `threadIdx.x` for this pass
+  const uint32_t gofs = block_exclusive_scan_256(hist[pass * kRadix + threadIdx.x], sm.tmp);
+  const int items = sort_items_for(n);
+  if (items == 16)
+    sort_pass_tiles<16>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
+                        timeout_flag);
+  else if (items == 8)
+    sort_pass_tiles<8>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
+                       timeout_flag);
+  else
+    sort_pass_tiles<4>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
+                       timeout_flag);
 }
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev,
@@ -250,7 +286,7 @@ void init_occupancy() {
 void prepare_sort_kernels() { init_occupancy(); }
 
 size_t radix_sort_scratch(int64_t n_max) {
-  const int64_t tiles = (n_max + kSortTileKeys - 1) / kSortTileKeys;
+  const int64_t tiles = sort_max_tiles(n_max);
   // hist [4][256] u32, counters [4] u32 (padded), lookback [tiles][256] u64, epoch u64, n u32
   return 4 * kRadix * 4 + 256 + (size_t)(tiles > 0 ? tiles : 1) * kRadix * 8 + 256;
 }
@@ -273,8 +309,7 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
   sort_histogram_kernel<<<(unsigned)hblocks, 256, 0, st>>>(keys, n_dev, n_max, passes, hist);
   aaag_status e = check_launch("sort_histogram");
   if (e != AAAG_OK) return e;
-  const int64_t tiles = (n_max + kSortTileKeys - 1) / kSortTileKeys;
-  const int64_t grid = std::min<int64_t>(tiles, (int64_t)g_sm_count * g_pass_blocks_per_sm);
+  const int64_t grid = std::min<int64_t>(sort_max_tiles(n_max), (int64_t)g_sm_count * g_pass_blocks_per_sm);
   uint32_t* kin = keys;
   uint32_t* vin = vals;
   uint32_t* kout = keys_alt;

@@ -3,7 +3,7 @@
 // fixed size, so the call needs nothing from the caller but the arrays to sort.
 //
 // Capacity: kStaticSortMax keys.  Every GPU that loads this library holds the
-// array (about 8.5 MB) until the process exits.
+// array (about 9 MB) until the process exits.
 #include <cstring>
 #include <mutex>
 
@@ -13,7 +13,7 @@ namespace aaag {
 namespace {
 
 constexpr int64_t kStaticSortMax = 1 << 20;
-constexpr int64_t kStaticTiles = (kStaticSortMax + kSortTileKeys - 1) / kSortTileKeys;
+constexpr int64_t kStaticTiles = sort_max_tiles(kStaticSortMax);
 
 // Layout (bytes):
 //   [0, 4096)              histograms, 4 passes x 256 x uint32
