@@ -9,11 +9,16 @@
 //   dF/dc_i     = alpha_i T_i
 //   dF/dalpha_i = c_i T_i - S_i / (1 - alpha_i)
 //   dA/dalpha_i = T_final / (1 - alpha_i)            (A = 1 - T_final)
-// No per-blend state is cached.  For each blended contributor the pixel's two
-// transformed planes are recomputed (Eq. 4-5), rho^2 = |num|^2/|d|^2 is
-// differentiated back to the rows t1, t2, t3 of T_view, and the 16 values
-// (dt1, dt2, dt3, dcolour, do_hat) are added to a per-Gaussian accumulator
-// with vector atomics.
+// No per-blend state is cached.  For a contributor blended at once (the
+// staged Gaussian of the current item), rho^2 = |num|^2/|d|^2 is
+// differentiated back to the staged plane coefficients: its 22 moments
+// (dL/dnum and dL/dd weighted by 1, x, y; do_hat; dcolour) are reduced across
+// the warp into a per-slot shared accumulator, converted once per (tile,
+// Gaussian) into gradients of the rows t1, t2, t3 of T_view.  A queued
+// contributor recomputes its planes (Eq. 4-5) from the record at release and
+// adds its 16 row gradients to the per-Gaussian accumulator with vector
+// atomics.  (Releases of one slot by many lanes at once are common, so
+// per-lane shared atomics into the slot accumulator serialise badly.)
 //
 // K7 (preprocess backward) is one thread per Gaussian: it recomputes the
 // forward preprocessing and applies the chain rule through T_view = Rv R S'
@@ -31,12 +36,13 @@ namespace aaag {
 namespace {
 
 // Per-slot accumulators of the fast path, in shared memory after TileSmem:
-// [kMoments][kTilePixels]:  dL/dN0, dL/dNx, dL/dNy, dL/dD0, dL/dDx, dL/dDy
+// [kTilePixels][kAccStride]:  dL/dN0, dL/dNx, dL/dNy, dL/dD0, dL/dDx, dL/dDy
 // (3 each, tile-relative plane coefficients of render_core.cuh), dL/do_hat,
 // dL/dcolour (3).
 constexpr int kMoments = 22;
 constexpr size_t kStageBytes = sizeof(TileSmem<IndexQueue>);
-constexpr size_t kBackwardSmemBytes = kStageBytes + sizeof(float) * kMoments * kTilePixels;
+constexpr int kAccStride = kMoments + 1;   // odd: slot-major rows fall in distinct banks
+constexpr size_t kBackwardSmemBytes = kStageBytes + sizeof(float) * kAccStride * kTilePixels;
 
 struct BackwardBlend {
   using Queue = IndexQueue;
@@ -78,8 +84,42 @@ struct BackwardBlend {
     return true;
   }
 
-  // queued contributor: its planes are recomputed at this pixel and the
-  // gradient goes straight to the Gaussian's accumulator
+  // moments of contributor (alpha a, raw alpha o_hat G) at this pixel from its
+  // num, d, 1/|d|^2 and rho^2; false when the pixel is done
+  __device__ __forceinline__ bool moments(float a, float4 c, float oh, float n0, float n1, float n2, float d0,
+                                          float d1, float d2, float inv, float rho2, float m[kMoments]) {
+    float dal, w;
+    if (!composite(a, c, dal, w)) return false;
+    const float G = __expf(-0.5f * rho2);
+    const float raw = oh * G;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) m[i] = 0.0f;
+    if (raw < kAlphaMax) {
+      const float drho2 = -0.5f * dal * raw;
+      const float sn = 2.0f * drho2 * inv;
+      const float sd = -2.0f * drho2 * rho2 * inv;
+      const float dn[3] = {sn * n0, sn * n1, sn * n2};
+      const float ddv[3] = {sd * d0, sd * d1, sd * d2};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        m[i] = dn[i];
+        m[3 + i] = x * dn[i];
+        m[6 + i] = y * dn[i];
+        m[9 + i] = ddv[i];
+        m[12 + i] = x * ddv[i];
+        m[15 + i] = y * ddv[i];
+      }
+      m[18] = dal * G;
+    }
+    m[19] = gr * w;
+    m[20] = gg * w;
+    m[21] = gb * w;
+    return true;
+  }
+  __device__ __forceinline__ void begin_batch(uint32_t, int) {}
+  __device__ __forceinline__ uint32_t payload(int k) const { return st->gid[k]; }
+  // queued contributor: its planes are recomputed at this pixel from the
+  // record and the gradient goes straight to the Gaussian's accumulator
   __device__ __forceinline__ void blend(float a, uint32_t gid) {
     const float4* r = reinterpret_cast<const float4*>(rec + gid);
     const float4 c = __ldg(r + 3);
@@ -119,75 +159,54 @@ struct BackwardBlend {
     atomicAdd(acc4 + 3, make_float4(gr * w, gg * w, gb * w, doh));
   }
 
-  // the staged Gaussian k: gradient moments stay in registers until the
-  // warp-level reduction at the end of item k
-  __device__ __forceinline__ uint32_t payload(int k) const { return st->gid[k]; }
+  // the staged Gaussian k: moments stay in registers until the warp-level
+  // reduction at the end of item k
   __device__ __forceinline__ void blend_new(float a, const EvalState& ev) {
     const float4 c = __ldg(reinterpret_cast<const float4*>(rec + st->gid[ev.k]) + 3);
-    float dal, w;
-    if (!composite(a, c, dal, w)) return;
-    const float G = __expf(-0.5f * ev.rho2);
-    const float raw = st->a[ev.k].w * G;
-    if (raw < kAlphaMax) {
-      const float drho2 = -0.5f * dal * raw;
-      const float sn = 2.0f * drho2 * ev.inv;
-      const float sd = -2.0f * drho2 * ev.rho2 * ev.inv;
-      const float dn[3] = {sn * ev.n0, sn * ev.n1, sn * ev.n2};
-      const float ddv[3] = {sd * ev.d0, sd * ev.d1, sd * ev.d2};
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        acc[i] = dn[i];
-        acc[3 + i] = x * dn[i];
-        acc[6 + i] = y * dn[i];
-        acc[9 + i] = ddv[i];
-        acc[12 + i] = x * ddv[i];
-        acc[15 + i] = y * ddv[i];
-      }
-      acc[18] = dal * G;
-    }
-    acc[19] = gr * w;
-    acc[20] = gg * w;
-    acc[21] = gb * w;
-    has = true;
+    if (moments(a, c, st->a[ev.k].w, ev.n0, ev.n1, ev.n2, ev.d0, ev.d1, ev.d2, ev.inv, ev.rho2, acc)) has = true;
   }
-
+  // Warp reduction of the 22 moments of item k by halving exchanges: at each
+  // level every lane keeps one half of its values and receives its partner's
+  // copy of that half, so after five levels lane i holds the warp total of
+  // moment i (31 shuffles instead of 5 per moment); lanes 0..21 then add
+  // their moment to slot k in one instruction.
   __device__ __forceinline__ void end_item(int k) {
     const unsigned any = __ballot_sync(0xffffffffu, has);
     if (!any) return;
-    if (!has) {
+    const int lane = threadIdx.x & 31;
+    float v[32];
 #pragma unroll
-      for (int i = 0; i < kMoments; ++i) acc[i] = 0.0f;
+    for (int i = 0; i < 32; ++i) v[i] = (i < kMoments && has) ? acc[i] : 0.0f;
+#pragma unroll
+    for (int h = 16; h > 0; h >>= 1) {
+      const bool upper = (lane & h) != 0;
+#pragma unroll
+      for (int i = 0; i < h; ++i) {
+        const float send = upper ? v[i] : v[i + h];
+        const float keep = upper ? v[i + h] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+      }
     }
-#pragma unroll
-    for (int i = 0; i < kMoments; ++i) {
-      float v = acc[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[i] = v;
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-      for (int i = 0; i < kMoments; ++i)
-        if (acc[i] != 0.0f) atomicAdd(&sacc[i * kTilePixels + k], acc[i]);
-    }
+    if (lane < kMoments && v[0] != 0.0f) atomicAdd(&sacc[k * kAccStride + lane], v[0]);
 #pragma unroll
     for (int i = 0; i < kMoments; ++i) acc[i] = 0.0f;
     has = false;
   }
 
+
   // block-converged: convert each staged Gaussian's moments to gradients of
   // its T_view rows, one set of vector atomics per (tile, Gaussian)
-  __device__ __forceinline__ void end_batch(uint32_t b0, int cnt) {
+  __device__ __forceinline__ void end_batch(uint32_t, int count) {
     __syncthreads();
     const int t = threadIdx.x;
-    if (t < cnt) {
+    if (t < count) {
       float m[kMoments];
       bool nz = false;
 #pragma unroll
       for (int i = 0; i < kMoments; ++i) {
-        m[i] = sacc[i * kTilePixels + t];
+        m[i] = sacc[t * kAccStride + i];
         nz |= m[i] != 0.0f;
-        sacc[i * kTilePixels + t] = 0.0f;
+        sacc[t * kAccStride + i] = 0.0f;
       }
       if (nz) {
         const uint32_t gid = st->gid[t];
@@ -243,7 +262,7 @@ render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restr
   const bool in_image = px < fc.W && py < fc.H;
   const size_t HW = (size_t)fc.W * fc.H;
   const size_t p = in_image ? (size_t)py * fc.W + px : 0;
-  for (int i = threadIdx.x; i < kMoments * kTilePixels; i += kTilePixels) sacc[i] = 0.0f;
+  for (int i = threadIdx.x; i < kAccStride * kTilePixels; i += kTilePixels) sacc[i] = 0.0f;
 
   BackwardBlend bl;
   bl.st = &s.st;

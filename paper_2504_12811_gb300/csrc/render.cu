@@ -50,6 +50,7 @@ struct ForwardBlend {
   }
   __device__ __forceinline__ uint32_t payload(int k) const { return st->gid[k]; }
   __device__ __forceinline__ void blend_new(float a, const EvalState& ev) { blend(a, st->gid[ev.k]); }
+  __device__ __forceinline__ void begin_batch(uint32_t, int) {}
 };
 
 // Render one tile of one frame (all threads of the block).

@@ -204,6 +204,7 @@ struct EvalState {
 //   void blend(float alpha, Queue::Payload);         blend a queued contributor
 //   void blend_new(float alpha, const EvalState&);   blend the staged Gaussian k
 //   Queue::Payload payload(int k);                   what a queued entry of k carries
+//   void begin_batch(uint32_t b0, int cnt);          pairs b0 .. b0+cnt-1 are staged
 // With CONVERGENT, every lane runs every iteration (no early exit from the
 // pair loop) and the Blender also provides
 //   void end_item(int k);                            warp-converged, after item k
@@ -238,6 +239,7 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kTilePixels, range.y - b0);
+    bl.begin_batch(b0, cnt);
     if (CONVERGENT || !bl.done) {
       for (int k = 0; k < cnt; ++k) {
         const float4 bq = s.b[k];
