@@ -32,10 +32,15 @@ sys.path.insert(0, ROOT)
 METRIC = "1080p frames/s @1M Gaussians (fwd)"  # fwd+bwd under "fwd_bwd", served p50/p99 under "serving"
 WORKLOAD = "scene1m: 1,000,000 Gaussians (64 clusters + 10% shell, SH 3), 1920x1080, 16 poses"
 
-# algorithmic FP32 operations per pixel x Gaussian evaluation in the render
-# kernel: 12 FMA (num, d) + 3 x 3 for |num|^2, |d|^2 (6 FMA, counted 2 ops) ...
-# see DESIGN.md "Render roofline" for the count.
-OPS_PER_EVAL = 36
+# Algorithmic FP32 operations per pixel x Gaussian evaluation of the render
+# kernel: the two affine 3-vectors num, d in (x, y) and their squared norms
+# (~24), the reciprocal and rho^2, exp2 and its scale, the alpha clamp and
+# compares (~3), t* (~4) and the blend (~8): about 40.
+OPS_PER_EVAL = 40
+# Mean DRAM bytes (read + write) of one render launch over the 16 poses of the
+# workload, from an ncu capture of this kernel version (dram__bytes_read.sum +
+# dram__bytes_write.sum, cold cache).
+RENDER_DRAM_BYTES = 16.64e6
 FP32_LANES_PER_SM = 128
 SMS = 152
 
@@ -406,7 +411,7 @@ def run_ours(args):
                     "backward_ms": float(fb_ms[:, 1].mean()), "steps": bwd_steps,
                     "replay_mismatch": int(st_b["replay_mismatch"])},
         "roofline": {"kernel": "render", "bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops, "traffic": RENDER_DRAM_BYTES,
                      "peak_source": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
                      "ops_per_evaluation": OPS_PER_EVAL},
         "hbm": {"preprocess_gbs": pre_gbs, "sort_gbs": sort_gbs, "peak_gbs": hbm_peak,

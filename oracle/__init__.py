@@ -10,8 +10,8 @@ method.
 The oracle is a plain, slow, obviously-correct restatement of what the paper
 computes, in float64 on the float32 inputs, with plain PyTorch CPU ops (so
 autograd gives the analytic gradient of the same definition).  Every function
-cites the section / equation it follows.  Readings of passages the paper
-leaves open are listed in DESIGN.md ("Readings of the paper").
+cites the section / equation it follows; where the paper leaves a choice
+open, the function states the reading it takes.
 
 Pins (tests/test_oracle_pins.py) tie each function to something other than
 itself: closed forms, library routines (scipy rotations and spherical
