@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-train", action="store_true", help="skip the 500k-Gaussian training-step timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--capacity", type=int, default=48 << 20)
     ap.add_argument("--serve", default="400:2,60:4",
@@ -107,6 +108,55 @@ def run_serving(args, dev):
             "plain_per_frame": dict(serve.latency_summary(lat_p, max(plain_wall, seconds), n_views),
                                     wall_s=plain_wall)})
     return out
+
+
+def run_train_step(args, dev, flush):
+    """Forward + backward of each of the 4 views of the 500k-Gaussian
+    training workload (1280x832, SH 3): the rendering work of one training
+    step over those views.  This scene is dense enough that the per-pixel
+    buffer overflows: the order is approximate there."""
+    import numpy as np
+    import torch
+    from paper_2504_12811_gb300 import aaag, scenes
+    t0 = time.time()
+    scene, cams = scenes.workload("train500k")
+    t_gen = time.time() - t0
+    W, H = cams[0].width, cams[0].height
+    ds = aaag.DeviceScene(scene, device=dev)
+    ws = aaag.Workspace(scene.n, W, H, 64 << 20, device=dev)
+    rgb = torch.empty(3, H, W, device=dev)
+    alpha = torch.empty(H, W, device=dev)
+    grads = [torch.empty_like(t) for t in (ds.means, ds.log_scales, ds.quats, ds.opacity_logits, ds.sh)]
+    gs = aaag.aaag_grads(*[t.data_ptr() for t in grads])
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    drgb = torch.randn(3, H, W, device=dev, generator=g)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    prm = aaag.make_params()
+    sc = ds.struct()
+    cc = [aaag.make_camera(c) for c in cams]
+
+    def step():
+        for c in cc:
+            aaag.aaag_render_frame(sc, c, prm, ws.handle, rgb.data_ptr(), alpha.data_ptr(), sptr)
+            aaag.aaag_render_backward(sc, ws.handle, rgb.data_ptr(), drgb.data_ptr(), None, gs, sptr)
+    for _ in range(2):
+        step()
+    st = aaag.stats(ws, check=False)
+    n = 8
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for k in range(n):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    return {"workload": "train500k: 500,000 Gaussians (uniform cube, SH 3), 4 views of 1280x832",
+            "ms_per_step": ms, "views_per_s": 4e3 / ms, "status": st["status"],
+            "pairs_last_view": st["n_pairs"], "misorders_last_view": st["misorders"],
+            "blended_last_view": st["blended"], "scene_generation_s": t_gen}
 
 
 def dist_env():
@@ -323,6 +373,33 @@ def run_ours(args):
     frames = args.steps * world
     value = frames / (total_ms / 1e3)
 
+    # ---- ablations (Sec. 5): the same frames with one switch each
+    ablation = {}
+    abl_steps = max(16, min(args.steps, 64))
+    for name, flags in (("full", 0), ("no_cull", aaag.AAAG_FLAG_NO_CULL),
+                        ("no_resort", aaag.AAAG_FLAG_NO_RESORT), ("no_filter", aaag.AAAG_FLAG_NO_FILTER),
+                        ("kbuffer", aaag.AAAG_FLAG_KBUFFER)):
+        p_abl = aaag.make_params(flags=flags)
+        def abl_frame(i):
+            aaag.aaag_preprocess(scene_struct, cams[i % len(cams)], p_abl, ws.handle, sptr)
+            aaag.aaag_cull(ws.handle, sptr)
+            aaag.aaag_sort(ws.handle, sptr)
+            aaag.aaag_render(ws.handle, rgb.data_ptr(), alpha.data_ptr(), sptr)
+        for i in range(3):
+            abl_frame(i)
+        ok = aaag.stats(ws, check=False)["status"] == "OK"
+        aev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(abl_steps)]
+        for k in range(abl_steps):
+            flush.zero_()
+            aev[k][0].record(stream)
+            abl_frame(k)
+            aev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in aev]))
+        ablation[name] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms, "status_ok": ok}
+    for name in ablation:
+        ablation[name]["vs_full"] = ablation[name]["ms_per_frame"] / ablation["full"]["ms_per_frame"]
+
     # ---- forward + backward (gradients w.r.t. every scene parameter)
     grads = [torch.empty_like(t) for t in (ds.means, ds.log_scales, ds.quats, ds.opacity_logits, ds.sh)]
     gstruct = aaag.aaag_grads(*[t.data_ptr() for t in grads])
@@ -407,6 +484,7 @@ def run_ours(args):
                       "evaluations": mean("evaluations"), "blended": mean("blended"),
                       "misorders": mean("misorders"), "tiles_tested": mean("tiles_tested")},
         "evals_per_s": float(np.sum(ev_by_step) / (total_ms / 1e3)),
+        "ablation": ablation,
         "fwd_bwd": {"value": fwd_bwd_fps, "unit": "frames/s", "forward_ms": float(fb_ms[:, 0].mean()),
                     "backward_ms": float(fb_ms[:, 1].mean()), "steps": bwd_steps,
                     "replay_mismatch": int(st_b["replay_mismatch"])},
@@ -424,6 +502,8 @@ def run_ours(args):
         "wall_s_timed": wall,
         "scene_generation_s": t_gen,
     }
+    if not args.no_train:
+        line["train_step"] = run_train_step(args, dev, flush)
     if args.serve:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

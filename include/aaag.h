@@ -81,6 +81,17 @@ typedef struct {
 /* Method parameters. */
 #define AAAG_FLAG_NO_FILTER 1u  /* ablation: no 3D smoothing filter (phi=1)  */
 #define AAAG_FLAG_NO_CULL   2u  /* ablation: keep every tile of the bounds   */
+/* ablation of the blending sort order (Sec. 3.1 'Blending Sort Order', the
+ * sort ablation of Sec. 5): pairs are keyed by the view depth of the mean
+ * (clamped to z_near) and contributors are blended in pair order, with no
+ * per-pixel re-sort */
+#define AAAG_FLAG_NO_RESORT 4u
+/* bounded-buffer approximate re-sort (the per-ray sorting the paper retains
+ * from hierarchical rasterisation): contributors wait in the 16-entry
+ * per-pixel buffer, which releases its nearest entry only when full and the
+ * rest at the end; no release by key, so the order is exact only while the
+ * buffer never fills */
+#define AAAG_FLAG_KBUFFER   8u
 typedef struct {
   float k;             /* filter size, Sec. 4: k = 0.3                       */
   float eps;           /* angle clamp epsilon of Sec. 3.3 Eq. 17, e.g. 1e-3  */

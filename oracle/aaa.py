@@ -321,7 +321,8 @@ def pixel_alphas(prep, rho2, tstar):
 def composite(alpha, tstar, contrib, rgb, bg):
     """Front-to-back compositing in exact per-pixel depth order (the order
     hierarchical sorting approximates, Sec. 3.1 'Blending Sort Order'):
-    contributors sorted by (t*, Gaussian index); C = sum c_i a_i T_i,
+    contributors sorted by (tstar, Gaussian index), tstar being the depth of
+    each maximum unless the caller passes another sort key; C = sum c_i a_i T_i,
     T_i = prod_{j<i} (1 - a_j); stop before the contributor that would take T
     below 1e-4.  Returns (RGB + T bg [P,3], final T [P], blended count [P])."""
     with torch.no_grad():
@@ -346,9 +347,13 @@ def composite(alpha, tstar, contrib, rgb, bg):
 
 
 def render_pixels(scene, cam, px, py, k: float = K_FILTER, chunk: int = 512,
-                  prep=None):
+                  prep=None, order: str = "tstar"):
     """RGB [P,3] and alpha [P] of the given pixels (plain definition: every
-    Gaussian tested against every pixel)."""
+    Gaussian tested against every pixel).  order="tstar" blends in exact
+    per-pixel order of the maxima; order="mean" is the sort ablation of
+    Sec. 5 (no per-ray sorting): contributors blended in the order of the view
+    depth of their means, clamped to z_near (reading: the same clamp as the
+    depth keys), ties by Gaussian index."""
     if prep is None:
         prep = prepare(scene, cam, k)
     px = np.asarray(px).reshape(-1)
@@ -359,7 +364,13 @@ def render_pixels(scene, cam, px, py, k: float = K_FILTER, chunk: int = 512,
     for i in range(0, px.size, step):
         rho2, tstar = ray_maximum(prep, px[i:i + step], py[i:i + step])
         alpha, contrib, _ = pixel_alphas(prep, rho2, tstar)
-        out, T, _ = composite(alpha, tstar, contrib, prep["rgb"], prep["view"].bg)
+        if order == "mean":
+            key = torch.clamp(prep["mu_view"][:, 2].detach(), min=prep["view"].znear).expand_as(tstar)
+        elif order == "tstar":
+            key = tstar
+        else:
+            raise ValueError(order)
+        out, T, _ = composite(alpha, key, contrib, prep["rgb"], prep["view"].bg)
         outs.append(out)
         Ts.append(T)
     out = torch.cat(outs) if outs else torch.zeros(0, 3, dtype=F64)
@@ -367,11 +378,11 @@ def render_pixels(scene, cam, px, py, k: float = K_FILTER, chunk: int = 512,
     return out, 1.0 - T
 
 
-def render(scene, cam, k: float = K_FILTER, prep=None):
+def render(scene, cam, k: float = K_FILTER, prep=None, order: str = "tstar"):
     """Full image: RGB [3,H,W] and alpha [H,W] (float64)."""
     W, H = int(cam.width), int(cam.height)
     py, px = np.mgrid[0:H, 0:W]
-    out, alpha = render_pixels(scene, cam, px.ravel(), py.ravel(), k, prep=prep)
+    out, alpha = render_pixels(scene, cam, px.ravel(), py.ravel(), k, prep=prep, order=order)
     return out.T.reshape(3, H, W), alpha.reshape(H, W)
 
 

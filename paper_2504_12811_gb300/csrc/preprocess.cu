@@ -307,7 +307,8 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev& s, const FrameCon
       const float3 A3p = A3 - a3c * ch;
       float t_lo = vz - sqrtf(tau_c * dot3(A3p, A3p)) + fminf(a3c, 0.0f) * tau_c / cn;
       t_lo -= 1e-5f * fabsf(t_lo) + 1e-6f;
-      const float zk = fmaxf(fmaxf(t_lo, z_lo), fc.znear);
+      // (sort ablation: the depth of the mean)
+      const float zk = (fc.flags & AAAG_FLAG_NO_RESORT) ? fmaxf(vz, fc.znear) : fmaxf(fmaxf(t_lo, z_lo), fc.znear);
       uint32_t dk = (__float_as_uint(zk) - fc.znear_bits) >> fc.depth_shift;
       const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
       dk = min(dk, dmax);

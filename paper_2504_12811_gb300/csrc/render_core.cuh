@@ -219,6 +219,10 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
   const int ox = tile_x * kTile, oy = tile_y * kTile;
   const float cxm = fc.cx - (float)ox, cym = fc.cy - (float)oy;
   const uint32_t wbit = 1u << (threadIdx.x >> 5);
+  // ablations: blend in pair order (no re-sort); release only when the
+  // buffer is full (no release by key)
+  const bool resort = !(fc.flags & AAAG_FLAG_NO_RESORT);
+  const bool by_key = !(fc.flags & AAAG_FLAG_KBUFFER);
   const float kInf = __int_as_float(0x7f800000);
   StageSmem& s = sm.st;
   SmemQueue<typename Blender::Queue> q;
@@ -262,13 +266,13 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
             const float raw = a.w * __expf(-0.5f * rho2);
             const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
             if (raw >= kAlphaMin && ts >= fc.znear) {
-              const float Lnext = s.L[k];
+              const float Lnext = by_key ? s.L[k] : -kInf;
               const float ca = fminf(raw, kAlphaMax);
               const EvalState ev{k, n0, n1, n2, d0, d1, d2, inv, rho2};
               // 1. queued entries in front of the new one that nothing later can precede
               while (q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext) q.release(bl);
               if (!bl.done) {
-                if (ts < Lnext) {
+                if (ts < Lnext || !resort) {
                   // 2. the new contributor, then the rest below L_next
                   bl.blend_new(ca, ev);
                   while (q.n > 0 && !bl.done && q.ft < Lnext) q.release(bl);

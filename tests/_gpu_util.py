@@ -75,9 +75,9 @@ def compare_image(gpu_rgb, gpu_alpha, ref_rgb, ref_alpha, ambiguous):
     }
 
 
-def oracle_image_and_mask(scene, cam):
-    prep = O.prepare(scene, cam)
-    rgb, alpha = O.render(scene, cam, prep=prep)
+def oracle_image_and_mask(scene, cam, k=O.K_FILTER, order="tstar"):
+    prep = O.prepare(scene, cam, k)
+    rgb, alpha = O.render(scene, cam, k, prep=prep, order=order)
     py, px = np.mgrid[0:cam.height, 0:cam.width]
     mask = []
     step = 2048

@@ -344,6 +344,36 @@ def test_two_gaussians_depth_order_and_index_independence():
     np.testing.assert_allclose(a, col[0] * al[0] + col[1] * al[1] * (1 - al[0]), rtol=1e-12)
 
 
+def test_mean_depth_order_ablation_closed_form():
+    # Sort ablation of Sec. 5: blending in the order of the means' depths
+    # instead of the maxima.  A is long and tilted in x-z, its mean off the
+    # ray, so its maximum along the ray lies in front of B's while its mean
+    # lies behind B's; the two orders composite A over B and B over A.
+    cam = scenes.Camera(np.eye(4, dtype=np.float32), 50.0, 50.0, 8.5, 6.5, 17, 13, bg=(0.1, 0.2, 0.3))
+    h = math.radians(-22.5)
+    qs = np.array([[math.cos(h), 0.0, math.sin(h), 0.0], [1.0, 0.0, 0.0, 0.0]], np.float32)
+    sc = one_gaussian_scene([[0.3, 0.0, 4.0], [0.0, 0.0, 3.85]], [[0.0, -1.5, -1.5], [-2.5, -2.5, -2.5]],
+                            q=qs, logit=1.0)
+    sc.sh[:, 0, :] = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 1.0]], np.float32)
+    p = O.prepare(sc, cam)
+    rho2, ts = O.ray_maximum(p, np.array([8]), np.array([6]))
+    alpha, contrib, _ = O.pixel_alphas(p, rho2, ts)
+    assert bool(contrib.all())
+    t = ts[0].numpy()
+    mz = p["mu_view"][:, 2].numpy()
+    assert t[0] < t[1] and mz[0] > mz[1]          # the two orders disagree
+    a = alpha[0].numpy()
+    col = p["rgb"].numpy()
+    bg = np.array([0.1, 0.2, 0.3], np.float32).astype(np.float64)
+    a_first = col[0] * a[0] + col[1] * a[1] * (1 - a[0]) + (1 - a[0]) * (1 - a[1]) * bg
+    b_first = col[1] * a[1] + col[0] * a[0] * (1 - a[1]) + (1 - a[0]) * (1 - a[1]) * bg
+    exact = O.render_pixels(sc, cam, [8], [6])[0][0].numpy()
+    mean = O.render_pixels(sc, cam, [8], [6], order="mean")[0][0].numpy()
+    np.testing.assert_allclose(exact, a_first, rtol=1e-12)
+    np.testing.assert_allclose(mean, b_first, rtol=1e-12)
+    assert np.abs(exact - mean).max() > 1e-3
+
+
 def test_early_termination_closed_form():
     # five coaxial Gaussians with o_hat = 0.95 at rho = 0: T = 0.05^k; the
     # fourth would take T below 1e-4, so exactly three are blended
