@@ -14,17 +14,18 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
 constexpr int kMaxShDegree = 3;
-constexpr int kSortItems = 16;            // keys per thread in a sort pass
+constexpr int kSortItems = 8;             // keys per thread in a sort pass
 constexpr int kSortThreads = 256;
-constexpr int kSortTileKeys = kSortItems * kSortThreads;   // 4096: the largest sort tile
-// Sorts of at least kSortWideKeys keys use 16 keys per thread; smaller ones 8
-// (at least half of it) or 4, so that small sorts still spread over every SM.
+constexpr int kSortTileKeys = kSortItems * kSortThreads;   // 2048: the largest sort tile
+// Sorts of at least kSortWideKeys / 2 keys use 8 keys per thread, smaller ones
+// 4, so that small sorts still spread over every SM (16 measured slower at
+// every size: fewer blocks per SM hide less of the memory latency).
 constexpr int64_t kSortWideKeys = 1 << 20;
 // Most look-back tiles that a sort of up to n keys uses.
 __host__ __device__ constexpr int64_t sort_max_tiles(int64_t n) {
-  return ((n < kSortWideKeys / 2 ? n : kSortWideKeys / 2) + 1023) / 1024 > (n + 4095) / 4096
+  return ((n < kSortWideKeys / 2 ? n : kSortWideKeys / 2) + 1023) / 1024 > (n + 2047) / 2048
              ? ((n < kSortWideKeys / 2 ? n : kSortWideKeys / 2) + 1023) / 1024
-             : (n + 4095) / 4096;
+             : (n + 2047) / 2048;
 }
 constexpr int kMaxTileBits = 16;          // at most 65536 tiles per image
 

@@ -3,7 +3,7 @@
 // minor).
 //
 // Onesweep structure: one histogram kernel reads every key once and counts
-// all digit positions; then one kernel per 8-bit digit ranks a 4096-key tile
+// all digit positions; then one kernel per 8-bit digit ranks a 1024- or 2048-key tile
 // per block (warp-level multisplit with __match_any_sync, preserving input
 // order), publishes its per-digit counts, resolves the exclusive prefix of
 // earlier tiles by decoupled look-back, and scatters through shared memory.
@@ -228,7 +228,7 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __
 // Keys per thread by problem size: small sorts use small tiles so that every
 // SM has work and the look-back chains stay short in time.
 __device__ __forceinline__ int sort_items_for(int64_t n) {
-  return n >= kSortWideKeys ? 16 : (n >= kSortWideKeys / 2 ? 8 : 4);
+  return n >= kSortWideKeys / 2 ? 8 : 4;
 }
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -246,10 +246,7 @@ sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
   // global exclusive offset of digit `threadIdx.x` for this pass
   const uint32_t gofs = block_exclusive_scan_256(hist[pass * kRadix + threadIdx.x], sm.tmp);
   const int items = sort_items_for(n);
-  if (items == 16)
-    sort_pass_tiles<16>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
-                        timeout_flag);
-  else if (items == 8)
+  if (items == 8)
     sort_pass_tiles<8>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
                        timeout_flag);
   else
