@@ -400,6 +400,20 @@ def run_ours(args):
     for name in ablation:
         ablation[name]["vs_full"] = ablation[name]["ms_per_frame"] / ablation["full"]["ms_per_frame"]
 
+    # ---- training sampling frequency (Eq. 5) of every Gaussian over 128 cameras
+    rng_v = np.random.default_rng(3)
+    from paper_2504_12811_gb300 import scenes as S
+    tcams = [aaag.make_camera(c) for c in S.orbit_cameras(rng_v, 128, 30.0, W, H, 60.0)]
+    vout = torch.empty(scene.n, device=dev)
+    aaag.aaag_vhat_train(ds.means.data_ptr(), scene.n, tcams, vout.data_ptr(), sptr)
+    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    v0.record(stream)
+    for _ in range(5):
+        aaag.aaag_vhat_train(ds.means.data_ptr(), scene.n, tcams, vout.data_ptr(), sptr)
+    v1.record(stream)
+    torch.cuda.synchronize()
+    vhat_ms = v0.elapsed_time(v1) / 5
+
     # ---- forward + backward (gradients w.r.t. every scene parameter)
     grads = [torch.empty_like(t) for t in (ds.means, ds.log_scales, ds.quats, ds.opacity_logits, ds.sh)]
     gstruct = aaag.aaag_grads(*[t.data_ptr() for t in grads])
@@ -511,6 +525,7 @@ def run_ours(args):
                       "misorders": mean("misorders"), "tiles_tested": mean("tiles_tested")},
         "evals_per_s": float(np.sum(ev_by_step) / (total_ms / 1e3)),
         "ablation": ablation,
+        "vhat_train": {"gaussians": scene.n, "cameras": len(tcams), "ms": vhat_ms},
         "fwd_bwd": {"value": fwd_bwd_fps, "unit": "frames/s", "forward_ms": float(fb_ms[:, 0].mean()),
                     "backward_ms": float(fb_ms[:, 1].mean()), "steps": bwd_steps,
                     "replay_mismatch": int(st_b["replay_mismatch"])},

@@ -335,6 +335,23 @@ aaag_status aaag_radix_sort_static(uint32_t* keys, uint32_t* vals, int64_t n,
                                    int32_t key_bits, cudaStream_t stream);
 
 /* --------------------------------------------------------------------------
+ * aaag_vhat_train -- the training sampling frequency of every Gaussian (Sec.
+ * 3.2, Eq. 5): v_train = max over the training cameras of f / d, f the
+ * camera's focal length in pixels (fx) and d the view depth of the mean.
+ * Reading: a camera counts when the mean lies beyond its near plane and
+ * projects inside its image (0 <= u <= width, 0 <= v <= height); a Gaussian
+ * that no camera sees gets +inf (no clamp of the filter).
+ *   means   device [n][3] float32 (the scene's means)
+ *   cams    host array of n_cams cameras (copied into the launches)
+ *   out     device [n] float32, written (the scene's vhat_train input)
+ * Asynchronous on `stream`; n = 0 or n_cams = 0 (all +inf) are allowed.
+ * Errors: INVALID_ARG (n < 0, n_cams < 0, null pointers, a non-finite or
+ * degenerate camera), CUDA.
+ * ------------------------------------------------------------------------ */
+aaag_status aaag_vhat_train(const float* means, int64_t n, const aaag_camera* cams, int32_t n_cams,
+                            float* out, cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
  * aaag_get_stats -- synchronises `stream` and copies the frame statistics to
  * *out (host).  Returns CAPACITY if the pair capacity overflowed, TIMEOUT if a
  * bounded device wait gave up, else OK.

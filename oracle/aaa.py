@@ -21,7 +21,7 @@ __all__ = [
     "mip_factor", "cutoff", "sh_basis", "sh_colour", "prepare", "pixel_rays",
     "ray_maximum", "pixel_alphas", "composite", "render_pixels", "render",
     "view_space_bounds", "frustum_constraints", "frustum_min_rho2",
-    "tile_min_rho2", "ambiguous_pixels", "scene_tensors",
+    "tile_min_rho2", "ambiguous_pixels", "scene_tensors", "training_sampling_frequency",
 ]
 
 F64 = torch.float64
@@ -99,6 +99,28 @@ def rotation_from_quaternion(q: torch.Tensor) -> torch.Tensor:
 # ---------------------------------------------------------------------------
 # Sec. 3.1 (Eq. 6-7) and Sec. 3.2 (Eq. 8-13): adaptive 3D smoothing filter
 # ---------------------------------------------------------------------------
+
+def training_sampling_frequency(means, cams) -> np.ndarray:
+    """Sec. 3.2, Eq. 5: v_train = max over the training cameras of f / d, f
+    the focal length in pixels (fx), d the view depth of the mean.  Reading:
+    a camera counts when the mean lies beyond its near plane and projects
+    inside its image (0 <= u <= W, 0 <= v <= H, pixel-centre convention of the
+    cameras); +inf when no camera sees the mean (no clamp).  float64."""
+    m = np.asarray(means, np.float64)
+    best = np.full(m.shape[0], -np.inf)
+    for c in cams:
+        V = np.asarray(c.viewmat, np.float64)
+        p = m @ V[:3, :3].T + V[:3, 3]
+        z = p[:, 2]
+        front = z > float(c.znear)
+        zs = np.where(front, z, 1.0)
+        u = float(c.fx) * p[:, 0] / zs + float(c.cx)
+        v = float(c.fy) * p[:, 1] / zs + float(c.cy)
+        seen = front & (u >= 0) & (u <= c.width) & (v >= 0) & (v <= c.height)
+        best = np.maximum(best, np.where(seen, float(c.fx) / zs, -np.inf))
+    best[best == -np.inf] = np.inf
+    return best
+
 
 def sampling_frequency(z_view: torch.Tensor, f: float, znear: float) -> torch.Tensor:
     """v_hat = f / d, d = view-space z of the mean (Sec. 3.1, Eq. 6).  The

@@ -96,6 +96,7 @@ SIGNATURES = [
                                   C.c_void_p, C.c_size_t, C.POINTER(C.c_int32), C.c_void_p]),
     ("aaag_radix_sort_static_capacity", C.c_int64, []),
     ("aaag_radix_sort_static", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
+    ("aaag_vhat_train", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("aaag_get_stats", C.c_int, [C.c_void_p, C.POINTER(aaag_stats), C.c_void_p]),
     ("aaag_last_error", C.c_char_p, []),
 ]
@@ -211,6 +212,13 @@ def aaag_radix_sort(keys, vals, keys_alt, vals_alt, n, key_bits, scratch, scratc
     _check(lib().aaag_radix_sort(keys, vals, keys_alt, vals_alt, n, key_bits, scratch, scratch_bytes,
                                  C.byref(alt), stream), "aaag_radix_sort")
     return int(alt.value)
+
+
+def aaag_vhat_train(means_ptr, n, cams, out_ptr, stream):
+    """cams: sequence of aaag_camera structs (host)."""
+    arr = (aaag_camera * max(len(cams), 1))(*cams)
+    _check(lib().aaag_vhat_train(means_ptr, n, C.cast(arr, C.c_void_p), len(cams), out_ptr, stream),
+           "aaag_vhat_train")
 
 
 def aaag_radix_sort_static_capacity():

@@ -193,6 +193,29 @@ def test_smoothed_covariance_is_sum():
     np.testing.assert_allclose(Sig_hat - Sig, kv[:, None, None] * np.eye(3), atol=1e-12)
 
 
+def test_training_sampling_frequency_closed_forms():
+    # Eq. 5: max over cameras of f / d among the cameras that see the mean
+    eye = np.eye(4, dtype=np.float32)
+    cam1 = scenes.Camera(eye, 100.0, 100.0, 32.0, 24.0, 64, 48)            # at the origin, looking +z
+    back = eye.copy()
+    back[2, 3] = 2.0                                                          # 2 units further back
+    cam2 = scenes.Camera(back, 150.0, 150.0, 32.0, 24.0, 64, 48)
+    m = np.array([[0.0, 0.0, 4.0],        # seen by both: max(100/4, 150/6)
+                  [0.0, 0.0, -1.0],       # behind cam1, in front of cam2 at depth 1
+                  [5.0, 0.0, 4.0],        # outside both images
+                  [0.0, 0.0, 0.1],        # before cam1's near plane; cam2 at depth 2.1
+                  [1.28, 0.0, 4.0]],      # u = 32 + 100 * 0.32 = 64 = W for cam1: on the border
+                 np.float32)
+    v = O.training_sampling_frequency(m, [cam1, cam2])
+    assert v[0] == pytest.approx(max(100 / 4, 150 / 6), rel=1e-12)
+    assert v[1] == pytest.approx(150 / 1.0, rel=1e-12)
+    assert np.isinf(v[2]) and v[2] > 0
+    assert v[3] == pytest.approx(150 / 2.1, rel=1e-6)
+    u2 = 32 + 150 * float(np.float32(1.28)) / 6.0                             # cam2 sees it too
+    assert u2 < 64 and v[4] == pytest.approx(max(100 / 4, 150 / 6), rel=1e-12)
+    assert np.all(np.isinf(O.training_sampling_frequency(m, [])))
+
+
 def test_sampling_frequency_cases():
     sc = random_scene(30, 8)
     cam = cam_at((0.0, 0.0, -5.0))
