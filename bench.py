@@ -378,7 +378,7 @@ def run_ours(args):
     abl_steps = max(16, min(args.steps, 64))
     for name, flags in (("full", 0), ("no_cull", aaag.AAAG_FLAG_NO_CULL),
                         ("no_resort", aaag.AAAG_FLAG_NO_RESORT), ("no_filter", aaag.AAAG_FLAG_NO_FILTER),
-                        ("kbuffer", aaag.AAAG_FLAG_KBUFFER)):
+                        ("kbuffer", aaag.AAAG_FLAG_KBUFFER), ("no_3d", aaag.AAAG_FLAG_EVAL_2D)):
         p_abl = aaag.make_params(flags=flags)
         def abl_frame(i):
             aaag.aaag_preprocess(scene_struct, cams[i % len(cams)], p_abl, ws.handle, sptr)

@@ -92,6 +92,14 @@ typedef struct {
  * rest at the end; no release by key, so the order is exact only while the
  * buffer never fills */
 #define AAAG_FLAG_KBUFFER   8u
+/* ablation without 3D evaluation (Sec. 5, 'w/o 3D'): each Gaussian is
+ * splatted in 2D, its filtered covariance projected with the Jacobian of the
+ * perspective map at the mean (EWA, no extra screen-space dilation); alpha =
+ * min(0.99, o_hat exp(-rho^2/2)) with rho^2 the 2D Mahalanobis distance, the
+ * depth of every contribution is the mean's view depth, the camera-inside
+ * rule is not applied.  Forward only: aaag_render_backward returns
+ * AAAG_ERR_UNSUPPORTED for a frame rendered with it. */
+#define AAAG_FLAG_EVAL_2D   16u
 typedef struct {
   float k;             /* filter size, Sec. 4: k = 0.3                       */
   float eps;           /* angle clamp epsilon of Sec. 3.3 Eq. 17, e.g. 1e-3  */

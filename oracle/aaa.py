@@ -22,6 +22,7 @@ __all__ = [
     "ray_maximum", "pixel_alphas", "composite", "render_pixels", "render",
     "view_space_bounds", "frustum_constraints", "frustum_min_rho2",
     "tile_min_rho2", "ambiguous_pixels", "scene_tensors", "training_sampling_frequency",
+    "ewa_splats", "splat_maximum",
 ]
 
 F64 = torch.float64
@@ -368,14 +369,52 @@ def composite(alpha, tstar, contrib, rgb, bg):
     return out, T, blended.sum(1)
 
 
+def ewa_splats(prep):
+    """Ablation without 3D evaluation (Sec. 5, 'w/o 3D'): every Gaussian as a
+    2D splat.  The filtered world covariance R diag(s_hat) R^T is taken to
+    view space (Rv . Rv^T) and projected with the Jacobian J of the
+    perspective map (fx x/z + cx, fy y/z + cy) at the view-space mean (the EWA
+    local affine approximation); reading: no extra screen-space dilation.
+    Returns the projected means [G,2] and the 2D covariances [G,2,2]."""
+    view = prep["view"]
+    Rv = view.Rv
+    S = torch.einsum("gij,gj,gkj->gik", prep["R"], prep["s_hat"], prep["R"])
+    Sv = Rv @ S @ Rv.T
+    x, y, z = prep["mu_view"].unbind(-1)
+    zero = torch.zeros_like(z)
+    J = torch.stack([torch.stack([view.fx / z, zero, -view.fx * x / z ** 2], -1),
+                     torch.stack([zero, view.fy / z, -view.fy * y / z ** 2], -1)], -2)   # [G,2,3]
+    cov2 = J @ Sv @ J.transpose(-1, -2)
+    mean2 = torch.stack([view.fx * x / z + view.cx, view.fy * y / z + view.cy], -1)
+    return mean2, cov2
+
+
+def splat_maximum(prep, px, py, splats=None):
+    """rho^2 of the 2D splats at the pixel centres [P,G] (squared
+    Mahalanobis distance in the 2D covariance) and the depth of each
+    contribution, the mean's view depth [P,G]."""
+    mean2, cov2 = splats if splats is not None else ewa_splats(prep)
+    a, b, c = cov2[:, 0, 0], cov2[:, 0, 1], cov2[:, 1, 1]
+    det = a * c - b * b                                  # inverse of [[a, b], [b, c]]
+    q = torch.stack([t64(np.asarray(px) + 0.5), t64(np.asarray(py) + 0.5)], -1)   # [P,2]
+    dx = q[:, :1] - mean2[:, 0].unsqueeze(0)                                        # [P,G]
+    dy = q[:, 1:] - mean2[:, 1].unsqueeze(0)
+    rho2 = (c * dx * dx - 2.0 * b * dx * dy + a * dy * dy) / det
+    tstar = prep["mu_view"][:, 2].unsqueeze(0).expand_as(rho2)
+    return rho2, tstar
+
+
 def render_pixels(scene, cam, px, py, k: float = K_FILTER, chunk: int = 512,
-                  prep=None, order: str = "tstar"):
+                  prep=None, order: str = "tstar", eval2d: bool = False):
     """RGB [P,3] and alpha [P] of the given pixels (plain definition: every
     Gaussian tested against every pixel).  order="tstar" blends in exact
     per-pixel order of the maxima; order="mean" is the sort ablation of
     Sec. 5 (no per-ray sorting): contributors blended in the order of the view
     depth of their means, clamped to z_near (reading: the same clamp as the
-    depth keys), ties by Gaussian index."""
+    depth keys), ties by Gaussian index.  eval2d=True is the ablation without
+    3D evaluation: alpha from the EWA splats (`ewa_splats`), depth the mean's,
+    and (reading) no camera-inside rule: a Gaussian is alive when o_hat >
+    1/255 and its mean lies beyond the near plane."""
     if prep is None:
         prep = prepare(scene, cam, k)
     px = np.asarray(px).reshape(-1)
@@ -383,9 +422,17 @@ def render_pixels(scene, cam, px, py, k: float = K_FILTER, chunk: int = 512,
     G = prep["mu"].shape[0]
     step = max(1, min(chunk, (1 << 24) // max(G, 1)))
     outs, Ts = [], []
+    if eval2d:
+        splats = ewa_splats(prep)
+        p2 = dict(prep)
+        p2["alive"] = (prep["o_hat"] > ALPHA_MIN) & (prep["mu_view"][:, 2] >= prep["view"].znear)
     for i in range(0, px.size, step):
-        rho2, tstar = ray_maximum(prep, px[i:i + step], py[i:i + step])
-        alpha, contrib, _ = pixel_alphas(prep, rho2, tstar)
+        if eval2d:
+            rho2, tstar = splat_maximum(prep, px[i:i + step], py[i:i + step], splats)
+            alpha, contrib, _ = pixel_alphas(p2, rho2, tstar)
+        else:
+            rho2, tstar = ray_maximum(prep, px[i:i + step], py[i:i + step])
+            alpha, contrib, _ = pixel_alphas(prep, rho2, tstar)
         if order == "mean":
             key = torch.clamp(prep["mu_view"][:, 2].detach(), min=prep["view"].znear).expand_as(tstar)
         elif order == "tstar":
@@ -400,11 +447,11 @@ def render_pixels(scene, cam, px, py, k: float = K_FILTER, chunk: int = 512,
     return out, 1.0 - T
 
 
-def render(scene, cam, k: float = K_FILTER, prep=None, order: str = "tstar"):
+def render(scene, cam, k: float = K_FILTER, prep=None, order: str = "tstar", eval2d: bool = False):
     """Full image: RGB [3,H,W] and alpha [H,W] (float64)."""
     W, H = int(cam.width), int(cam.height)
     py, px = np.mgrid[0:H, 0:W]
-    out, alpha = render_pixels(scene, cam, px.ravel(), py.ravel(), k, prep=prep, order=order)
+    out, alpha = render_pixels(scene, cam, px.ravel(), py.ravel(), k, prep=prep, order=order, eval2d=eval2d)
     return out.T.reshape(3, H, W), alpha.reshape(H, W)
 
 
@@ -564,7 +611,7 @@ def tile_min_rho2(prep, gauss_idx, tile_x, tile_y, near: bool = True):
 # pixels where float32 rounding can legitimately flip a discrete decision
 # ---------------------------------------------------------------------------
 
-def ambiguous_pixels(prep, px, py, rel_alpha=2e-5, rel_t=2e-6, rel_tau=1e-4, swap=2e-4):
+def ambiguous_pixels(prep, px, py, rel_alpha=2e-5, rel_t=2e-6, rel_tau=1e-4, swap=2e-4, eval2d=False):
     """Pixels whose result depends on a decision that float32 evaluation may
     take differently from float64 (test tolerance logic, not part of the
     method):
@@ -574,17 +621,23 @@ def ambiguous_pixels(prep, px, py, rel_alpha=2e-5, rel_t=2e-6, rel_tau=1e-4, swa
         rel_tau of its threshold, touching the pixel;
       * two depth-adjacent contributors whose t* differ by less than rel_t
         (relative) and whose swap would change the pixel by more than `swap`
-        (swapping a before b changes C by T_a alpha_a alpha_b (c_a - c_b))."""
-    rho2, tstar = ray_maximum(prep, px, py)
-    raw = prep["o_hat"].unsqueeze(0) * torch.exp(-0.5 * rho2)
+        (swapping a before b changes C by T_a alpha_a alpha_b (c_a - c_b)).
+    eval2d: the same for the 2D-splat ablation (no camera-inside test)."""
     view = prep["view"]
-    live = prep["alive"].unsqueeze(0)
+    if eval2d:
+        rho2, tstar = splat_maximum(prep, px, py)
+        live = ((prep["o_hat"] > ALPHA_MIN) & (prep["mu_view"][:, 2] >= view.znear)).unsqueeze(0)
+    else:
+        rho2, tstar = ray_maximum(prep, px, py)
+        live = prep["alive"].unsqueeze(0)
+    raw = prep["o_hat"].unsqueeze(0) * torch.exp(-0.5 * rho2)
     near_alpha = (raw - ALPHA_MIN).abs() < rel_alpha * ALPHA_MIN
     contrib = live & (raw >= ALPHA_MIN) & (tstar >= view.znear)
     near_z = ((tstar - view.znear).abs() < rel_t * view.znear) & (raw >= ALPHA_MIN * (1 - rel_alpha))
     uu = (prep["u_cam"] ** 2).sum(-1)
-    edge_g = ((uu - prep["tau"]).abs() < rel_tau * prep["tau"].abs()) | \
-             ((prep["o_hat"] - ALPHA_MIN).abs() < rel_tau * ALPHA_MIN)
+    edge_g = (prep["o_hat"] - ALPHA_MIN).abs() < rel_tau * ALPHA_MIN
+    if not eval2d:
+        edge_g = edge_g | ((uu - prep["tau"]).abs() < rel_tau * prep["tau"].abs())
     touched = raw >= ALPHA_MIN * (1 - rel_alpha)
     flag = ((near_alpha | near_z) & (live | edge_g.unsqueeze(0))).any(1)
     flag |= (touched & edge_g.unsqueeze(0)).any(1)

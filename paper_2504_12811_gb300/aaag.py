@@ -15,11 +15,13 @@ import numpy as np
 from .build import LIB_PATH
 
 AAAG_OK = 0
+AAAG_ERR_INVALID_ARG, AAAG_ERR_CAPACITY, AAAG_ERR_CUDA, AAAG_ERR_TIMEOUT, AAAG_ERR_UNSUPPORTED = 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CAPACITY", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED"}
 AAAG_FLAG_NO_FILTER = 1
 AAAG_FLAG_NO_CULL = 2
 AAAG_FLAG_NO_RESORT = 4
 AAAG_FLAG_KBUFFER = 8
+AAAG_FLAG_EVAL_2D = 16
 AAAG_STAGE_PREPROCESS, AAAG_STAGE_CULL, AAAG_STAGE_SORT, AAAG_STAGE_RENDER = 1, 2, 4, 8
 
 

@@ -421,6 +421,10 @@ aaag_status aaag_render_backward(const aaag_scene* scene, aaag_workspace* ws, co
     set_error("aaag_render_backward: null gradient array");
     return AAAG_ERR_INVALID_ARG;
   }
+  if (ws->fc.flags & AAAG_FLAG_EVAL_2D) {
+    set_error("aaag_render_backward: the 2D-evaluation ablation is forward only");
+    return AAAG_ERR_UNSUPPORTED;
+  }
   if (cudaMemsetAsync(ws->stats + kStatReplayMismatch, 0, 8, stream) != cudaSuccess)
     return check_launch("backward memset");
   return launch_render_backward(scene_dev(scene), ws, rgb, dL_drgb, dL_dalpha, grads, stream);

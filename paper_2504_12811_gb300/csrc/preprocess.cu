@@ -118,6 +118,40 @@ __device__ __forceinline__ bool pixel_range(float p1, float p2, int size, int& i
   return i0 <= i1;
 }
 
+// Ablation without 3D evaluation (Sec. 5): the Gaussian is splatted in 2D.
+// Its filtered view-space covariance A A^T (A = Rv R S') is projected with
+// the Jacobian J of the perspective map at the mean (EWA), Sigma' = (J A)(J A)^T
+// (2x2, no extra screen-space dilation), and the pixel (x, y) sees
+// rho^2 = D^T Sigma'^-1 D, D = (x, y) - projected mean, at depth t* = z.
+// With the rows (A1' | x_v), (A2' | y_v), (0 | z_v), the plane form of
+// Eq. 4-5 used by every later stage gives exactly this: n1 = fx A1',
+// h1 = z (m_x - x), n2 = fy A2', h2 = z (m_y - y), so d = n1 x n2 is constant,
+// t* = G.d/|d|^2 = z and |num|^2/|d|^2 = |L^T D|^2 when A1' = |d| (l21, l22, 0)
+// / (z fx), A2' = -|d| (l11, 0, 0) / (z fy), |d| = z^2 / (l11 l22), with
+// L L^T = Sigma'^-1 (Cholesky).  Writes the rows and the pixel-centre ranges
+// of the ellipse rho^2 <= tau; false when the splat is degenerate or off the
+// image.
+__device__ __forceinline__ bool ewa_record(float3 A1, float3 A2, float3 A3, float vx, float vy, float vz,
+                                           float tau_c, const FrameConst& fc, float4& t1, float4& t2,
+                                           float4& t3, int& ix0, int& ix1, int& iy0, int& iy1) {
+  const float iz = 1.0f / vz;
+  const float3 P1 = (fc.fx * iz) * (A1 - (vx * iz) * A3);
+  const float3 P2 = (fc.fy * iz) * (A2 - (vy * iz) * A3);
+  const float a = dot3(P1, P1), b = dot3(P1, P2), c = dot3(P2, P2);
+  const float det = fmaf(a, c, -b * b);
+  if (!(det > 0.0f) || !(c > 0.0f) || !isfinite(det)) return false;
+  const float l11 = sqrtf(c / det), l21 = -b / sqrtf(c * det), l22 = rsqrtf(c);
+  const float dn = vz * vz / (l11 * l22);
+  const float s1 = dn / (vz * fc.fx), s2 = -dn / (vz * fc.fy);
+  t1 = make_float4(s1 * l21, s1 * l22, 0.0f, vx);
+  t2 = make_float4(s2 * l11, 0.0f, 0.0f, vy);
+  t3 = make_float4(0.0f, 0.0f, 0.0f, vz);
+  const float mx = fmaf(fc.fx, vx * iz, fc.cx), my = fmaf(fc.fy, vy * iz, fc.cy);
+  const float hx = sqrtf(tau_c * a), hy = sqrtf(tau_c * c);
+  const float ex = 0.01f + 1e-5f * fabsf(mx), ey = 0.01f + 1e-5f * fabsf(my);
+  return pixel_range(mx - hx - ex, mx + hx + ex, fc.W, ix0, ix1) && pixel_range(my - hy - ey, my + hy + ey, fc.H, iy0, iy1);
+}
+
 // Activations, view-space mean and filtered variances of Gaussian i (the part
 // every Gaussian needs before the early test).
 struct Basic {
@@ -165,6 +199,8 @@ __device__ __forceinline__ Basic load_basic(const SceneDev& s, const FrameConst&
 // sphere wholly outside one side plane of the image frustum or in front of
 // z_near holds no visible point.
 __device__ __forceinline__ bool may_be_visible(const Basic& b, const FrameConst& fc) {
+  // the EWA splat of the 2D-evaluation ablation is not bounded by the sphere
+  if (fc.flags & AAAG_FLAG_EVAL_2D) return b.vz >= fc.znear && b.opac > kAlphaMin;
   const float tau_max = 2.0f * logf(fmaxf(b.opac * 255.0f, 1.0f));
   const float rad = fmaf(sqrtf(inflate_tau(tau_max) * fmaxf(b.hx, fmaxf(b.hy, b.hz))), 1.001f, 1e-6f);
   bool near_view = b.vz + rad >= fc.znear && b.opac > kAlphaMin;
@@ -244,10 +280,14 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev& s, const FrameCon
            axis_bounds(A2, A3, vy, vz, tau_c, fc.fy, fc.cy, fc.eps, py1, py2) &&
            pixel_range(px1, px2, fc.W, ix0, ix1) && pixel_range(py1, py2, fc.H, iy0, iy1);
     }
-    const float4 t1 = make_float4(A[0], A[1], A[2], vx);
-    const float4 t2 = make_float4(A[3], A[4], A[5], vy);
-    const float4 t3 = make_float4(A[6], A[7], A[8], vz);
-    if (ok) {
+    float4 t1 = make_float4(A[0], A[1], A[2], vx);
+    float4 t2 = make_float4(A[3], A[4], A[5], vy);
+    float4 t3 = make_float4(A[6], A[7], A[8], vz);
+    const bool eval2d = (fc.flags & AAAG_FLAG_EVAL_2D) != 0;
+    if (eval2d) {
+      // ablation without 3D evaluation: the record encodes the EWA splat
+      ok = vz >= fc.znear && ewa_record(A1, A2, A3, vx, vy, vz, tau_c, fc, t1, t2, t3, ix0, ix1, iy0, iy1);
+    } else if (ok) {
       // whole-image frustum cull (Sec. 3.4, last paragraph)
       const float W = (float)fc.W, H = (float)fc.H;
       ok = (z_lo < fc.znear)
@@ -307,15 +347,16 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev& s, const FrameCon
       const float3 A3p = A3 - a3c * ch;
       float t_lo = vz - sqrtf(tau_c * dot3(A3p, A3p)) + fminf(a3c, 0.0f) * tau_c / cn;
       t_lo -= 1e-5f * fabsf(t_lo) + 1e-6f;
-      // (sort ablation: the depth of the mean)
-      const float zk = (fc.flags & AAAG_FLAG_NO_RESORT) ? fmaxf(vz, fc.znear) : fmaxf(fmaxf(t_lo, z_lo), fc.znear);
+      // (sort and 2D-evaluation ablations: the depth of the mean)
+      const float zk = (fc.flags & (AAAG_FLAG_NO_RESORT | AAAG_FLAG_EVAL_2D)) ? fmaxf(vz, fc.znear)
+                                                                             : fmaxf(fmaxf(t_lo, z_lo), fc.znear);
       uint32_t dk = (__float_as_uint(zk) - fc.znear_bits) >> fc.depth_shift;
       const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
       dk = min(dk, dmax);
       // tau_rho, negated when the front of the ellipsoid reaches znear (the
       // tile test then truncates the frustum at the near plane)
       aux[i] = make_uint4((uint32_t)ix0 | ((uint32_t)iy0 << 16), (uint32_t)ix1 | ((uint32_t)iy1 << 16),
-                          __float_as_uint(z_lo < fc.znear ? -tau : tau), dk);
+                          __float_as_uint(z_lo < fc.znear && !eval2d ? -tau : tau), dk);
       const uint32_t ntiles = (uint32_t)((ix1 / kTile) - (ix0 / kTile) + 1) *
                               (uint32_t)((iy1 / kTile) - (iy0 / kTile) + 1);
       chunks[i] = (ntiles + 31u) / 32u;

@@ -75,13 +75,13 @@ def compare_image(gpu_rgb, gpu_alpha, ref_rgb, ref_alpha, ambiguous):
     }
 
 
-def oracle_image_and_mask(scene, cam, k=O.K_FILTER, order="tstar"):
+def oracle_image_and_mask(scene, cam, k=O.K_FILTER, order="tstar", eval2d=False):
     prep = O.prepare(scene, cam, k)
-    rgb, alpha = O.render(scene, cam, k, prep=prep, order=order)
+    rgb, alpha = O.render(scene, cam, k, prep=prep, order=order, eval2d=eval2d)
     py, px = np.mgrid[0:cam.height, 0:cam.width]
     mask = []
     step = 2048
     fx, fy = px.ravel(), py.ravel()
     for i in range(0, fx.size, step):
-        mask.append(O.ambiguous_pixels(prep, fx[i:i + step], fy[i:i + step]).numpy())
+        mask.append(O.ambiguous_pixels(prep, fx[i:i + step], fy[i:i + step], eval2d=eval2d).numpy())
     return prep, rgb, alpha, np.concatenate(mask).reshape(cam.height, cam.width)

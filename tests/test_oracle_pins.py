@@ -397,6 +397,33 @@ def test_mean_depth_order_ablation_closed_form():
     assert np.abs(exact - mean).max() > 1e-3
 
 
+def test_ewa_splat_closed_form():
+    # Ablation without 3D evaluation: for an isotropic filtered variance
+    # s_hat, Sigma' = s_hat J J^T with J the perspective Jacobian at the mean;
+    # for a mean at (x, 0, z): Sigma'_xx = s_hat fx^2 (1/z^2 + x^2/z^4),
+    # Sigma'_yy = s_hat fy^2 / z^2, Sigma'_xy = 0.
+    cam = scenes.Camera(np.eye(4, dtype=np.float32), 60.0, 50.0, 8.5, 6.5, 17, 13)
+    sc = one_gaussian_scene([[0.5, 0.0, 4.0]], [[-1.5, -1.5, -1.5]], logit=1.0)
+    p = O.prepare(sc, cam)
+    sh = float(p["s_hat"][0, 0])
+    assert np.allclose(p["s_hat"].numpy(), sh)
+    mean2, cov2 = O.ewa_splats(p)
+    x, z = float(np.float32(0.5)), 4.0
+    np.testing.assert_allclose(cov2[0].numpy(), [[sh * 60.0 ** 2 * (1 / z ** 2 + x ** 2 / z ** 4), 0.0],
+                                                 [0.0, sh * 50.0 ** 2 / z ** 2]], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(mean2[0].numpy(), [60.0 * x / z + 8.5, 6.5], rtol=1e-12)
+    # alpha at a pixel: o_hat exp(-rho^2/2) with rho^2 the 2D Mahalanobis distance
+    px, py = 13, 9
+    d = np.array([px + 0.5 - mean2[0, 0].item(), py + 0.5 - 6.5])
+    rho2 = d[0] ** 2 / cov2[0, 0, 0].item() + d[1] ** 2 / cov2[0, 1, 1].item()
+    r2, ts = O.splat_maximum(p, np.array([px]), np.array([py]))
+    assert r2[0, 0].item() == pytest.approx(rho2, rel=1e-12)
+    assert ts[0, 0].item() == pytest.approx(4.0, rel=1e-12)
+    rgb, alpha = O.render_pixels(sc, cam, [px], [py], eval2d=True)
+    a = min(0.99, p["o_hat"][0].item() * math.exp(-0.5 * rho2))
+    assert alpha[0].item() == pytest.approx(a if a >= 1 / 255 else 0.0, rel=1e-12)
+
+
 def test_early_termination_closed_form():
     # five coaxial Gaussians with o_hat = 0.95 at rho = 0: T = 0.05^k; the
     # fourth would take T below 1e-4, so exactly three are blended
