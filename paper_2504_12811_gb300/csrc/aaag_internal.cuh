@@ -78,14 +78,17 @@ enum StatSlot : int {
   kStatOverflow = 6,
   kStatTimeout = 7,
   kStatCandidates = 8,     // uint32: Gaussians that passed the early preprocessing test
-  kStatFrameReset = 9,     // slots below this one are cleared at the start of every frame
-  kStatSortEpoch = 13,
-  kStatChunks = 9,         // chunks of 32 candidate tiles (K2 work items)
-  kStatReplayMismatch = 10,// pixels whose backward replay blended a different count
-  kStatBatchCounter = 11,  // uint32 work-item counter of the batched render
-  kStatChunksClipped = 14, // uint32: chunk count clipped to the chunk capacity
-  kStatPairsClipped = 15,  // uint32: pair count clipped to the pair capacity
-  kStatCount = 16
+  kStatCullTileA = 9,      // uint32 tile counters of the cull's look-back kernels
+  kStatCullTileB = 10,
+  kStatChunks = 11,        // chunks of 32 candidate tiles (K2 work items)
+  kStatChunksClipped = 12, // uint32: chunk count clipped to the chunk capacity
+  kStatPairsClipped = 13,  // uint32: pair count clipped to the pair capacity
+  kStatFrameReset = 14,    // slots below this one are cleared at the start of every frame
+  kStatReplayMismatch = 14,// pixels whose backward replay blended a different count
+  kStatBatchCounter = 15,  // uint32 work-item counter of the batched render
+  kStatSortEpoch = 16,
+  kStatFrameEpoch = 17,    // bumped by every frame's constants: tags the cull look-back words
+  kStatCount = 18
 };
 
 }  // namespace aaag
@@ -108,9 +111,8 @@ struct aaag_workspace {
   uint32_t* offsets;             // [n] exclusive prefix of counts
   int64_t chunk_capacity;
   uint32_t* chunk_owner;         // [chunk_capacity] Gaussian of each chunk
-  uint32_t* chunk_mask;          // [chunk_capacity] kept-tile ballot of each chunk
-  uint32_t* chunk_pair_offsets;  // [chunk_capacity] first pair of each chunk
-  unsigned long long* scan_partials;   // per scan block
+  uint32_t* chunk_mask;          // [chunk_capacity] needed-tile ballot of each chunk
+  unsigned long long* cull_lookback;   // look-back words of the cull's scans
   uint32_t* keys[2];
   uint32_t* vals[2];
   uint32_t* sort_hist;           // [4][256]
@@ -125,7 +127,6 @@ struct aaag_workspace {
   aaag::FrameConst* fc_dev;       // device copy read by the kernels
   bool have_frame;
   int sorted_in_alt;             // which buffer holds the sorted pairs
-  int64_t n_scan_blocks;
   int64_t n_sort_tiles;
 };
 
@@ -140,6 +141,8 @@ aaag_status check_launch(const char* what);
 // kernel launchers (one per translation unit)
 aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st);
+void prepare_cull_kernels();
+int64_t cull_lookback_words(int64_t n, int64_t chunk_cap);
 aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st);
 aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, float* const* alpha, int n,

@@ -35,7 +35,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t records, aux, cand, counts, offsets, partials, owner, mask, pofs, keys0, keys1, vals0, vals1, hist, counters,
+  size_t records, aux, cand, counts, offsets, owner, mask, cull_lb, keys0, keys1, vals0, vals1, hist, counters,
       lookback, ranges, final_T, n_blended, stats, grad, fc, total;
 };
 
@@ -54,7 +54,6 @@ Layout layout_of(int64_t n, int w, int h, int64_t cap) {
     return at;
   };
   const int64_t ccap = chunk_capacity_of(n, cap);
-  const int64_t nsb = (std::max(n, ccap) + 4095) / 4096 + 1;
   const int64_t nst = sort_max_tiles(cap) + 1;
   const size_t ntiles = (size_t)tiles_of(w) * tiles_of(h);
   L.records = take((size_t)n * sizeof(Record));
@@ -62,10 +61,9 @@ Layout layout_of(int64_t n, int w, int h, int64_t cap) {
   L.cand = take((size_t)n * 4);
   L.counts = take((size_t)n * 4);
   L.offsets = take((size_t)n * 4);
-  L.partials = take((size_t)nsb * 8);
   L.owner = take((size_t)ccap * 4);
   L.mask = take((size_t)ccap * 4);
-  L.pofs = take((size_t)ccap * 4);
+  L.cull_lb = take((size_t)cull_lookback_words(n, ccap) * 8);
   L.keys0 = take((size_t)cap * 4);
   L.keys1 = take((size_t)cap * 4);
   L.vals0 = take((size_t)cap * 4);
@@ -166,7 +164,12 @@ __global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
 // Frame constants are a kernel parameter here and device memory for every
 // other kernel of the frame: a captured frame graph is re-aimed at a new
 // camera by updating this one node.
-__global__ void set_frame_kernel(FrameConst* dst, FrameConst v) { *dst = v; }
+// Frame constants to device memory; the frame epoch tags this frame's cull
+// look-back words.
+__global__ void set_frame_kernel(FrameConst* dst, FrameConst v, unsigned long long* frame_epoch) {
+  *dst = v;
+  *frame_epoch += 1ull;
+}
 
 SceneDev scene_dev(const aaag_scene* scene) {
   SceneDev s;
@@ -260,11 +263,10 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
   w->candidates = reinterpret_cast<uint32_t*>(b + L.cand);
   w->counts = reinterpret_cast<uint32_t*>(b + L.counts);
   w->offsets = reinterpret_cast<uint32_t*>(b + L.offsets);
-  w->scan_partials = reinterpret_cast<unsigned long long*>(b + L.partials);
+  w->cull_lookback = reinterpret_cast<unsigned long long*>(b + L.cull_lb);
+  w->chunk_mask = reinterpret_cast<uint32_t*>(b + L.mask);
   w->chunk_capacity = chunk_capacity_of(n, pair_capacity);
   w->chunk_owner = reinterpret_cast<uint32_t*>(b + L.owner);
-  w->chunk_mask = reinterpret_cast<uint32_t*>(b + L.mask);
-  w->chunk_pair_offsets = reinterpret_cast<uint32_t*>(b + L.pofs);
   w->keys[0] = reinterpret_cast<uint32_t*>(b + L.keys0);
   w->keys[1] = reinterpret_cast<uint32_t*>(b + L.keys1);
   w->vals[0] = reinterpret_cast<uint32_t*>(b + L.vals0);
@@ -278,12 +280,12 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
   w->stats = reinterpret_cast<unsigned long long*>(b + L.stats);
   w->grad_acc = reinterpret_cast<float4*>(b + L.grad);
   w->fc_dev = reinterpret_cast<FrameConst*>(b + L.fc);
-  w->n_scan_blocks = (n + 4095) / 4096;
   w->n_sort_tiles = sort_max_tiles(pair_capacity);
   // the look-back epoch lives in the stats block and must start defined; the
   // look-back words are cleared once so that no stale word can match an epoch
   if (cudaMemset(w->stats, 0, kStatCount * 8) != cudaSuccess ||
-      cudaMemset(w->sort_lookback, 0, (size_t)(w->n_sort_tiles + 1) * 256 * 8) != cudaSuccess) {
+      cudaMemset(w->sort_lookback, 0, (size_t)(w->n_sort_tiles + 1) * 256 * 8) != cudaSuccess ||
+      cudaMemset(w->cull_lookback, 0, (size_t)cull_lookback_words(n, w->chunk_capacity) * 8) != cudaSuccess) {
     std::free(w);
     return check_launch("workspace_init memset");
   }
@@ -292,6 +294,7 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
   prepare_render_kernels();
   prepare_backward_kernels();
   prepare_sort_kernels();
+  prepare_cull_kernels();
   *ws = w;
   return AAAG_OK;
 }
@@ -361,7 +364,7 @@ aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, 
   ws->fc = fc;
   ws->have_frame = true;
   ws->sorted_in_alt = 0;
-  set_frame_kernel<<<1, 1, 0, stream>>>(ws->fc_dev, fc);
+  set_frame_kernel<<<1, 1, 0, stream>>>(ws->fc_dev, fc, ws->stats + kStatFrameEpoch);
   e = check_launch("set_frame");
   if (e != AAAG_OK) return e;
   // reset per-frame statistics (keep the sort epoch)
@@ -635,7 +638,8 @@ aaag_status aaag_graph_launch(aaag_graph* g, const aaag_camera* camera, cudaStre
   aaag_status e = make_frame(camera, g->has_params ? &g->params : nullptr, g->sh_degree, ws, &fc);
   if (e != AAAG_OK) return e;
   FrameConst* dst = ws->fc_dev;
-  void* args[2] = {&dst, &fc};
+  unsigned long long* epoch = ws->stats + kStatFrameEpoch;
+  void* args[3] = {&dst, &fc, &epoch};
   cudaKernelNodeParams p = g->frame_params;
   p.kernelParams = args;
   p.extra = nullptr;

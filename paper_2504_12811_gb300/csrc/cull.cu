@@ -4,16 +4,24 @@
 // Work is balanced in chunks of 32 candidate tiles: the rectangle of a visible
 // Gaussian (from K1) is cut into ceil(tiles / 32) chunks, so a Gaussian that
 // covers the whole screen becomes hundreds of independent warps instead of one
-// long serial loop.
-//   1. exclusive scan of the per-Gaussian chunk counts (written by K1)
-//   2. expand: each Gaussian writes its index into its chunks' owner slots
-//   3. test: one warp per chunk, one lane per tile; the warp ballot of kept
-//      tiles is stored (32-bit mask per chunk)
-//   4. exclusive scan of the mask popcounts -> pair offset of each chunk
-//   5. emit: one warp per chunk writes its pairs contiguously
+// long serial loop.  Three kernels; A and C are single passes with decoupled
+// look-back over tiles taken in order from an atomic counter:
+//   A. chunk_offsets_kernel: tiles of 2048 Gaussians; exclusive scan of the
+//      per-Gaussian chunk counts (written by K1) -> each Gaussian's first
+//      chunk, and each Gaussian writes its index into its chunks' owner slots.
+//   B. cull_test_kernel: one warp per chunk (grid-stride), one lane per tile;
+//      the ballot of the needed tiles is stored per chunk.
+//   C. cull_emit_kernel: tiles of 256 chunks; the tile's pair count is
+//      resolved into its global pair offset by look-back, and its warps write
+//      the pairs.
 // Pairs therefore land at deterministic positions: Gaussian order, then
-// rectangle row-major tile order.  Chunk and pair counts stay on the device;
-// the kernels loop over them with grid-stride warps.
+// rectangle row-major tile order.  Chunk and pair counts stay on the device.
+//
+// Look-back words are 64-bit: (frame epoch, 24 bits) << 40 | flag << 38 |
+// value (38 bits); the epoch is bumped once per frame by the kernel that
+// writes the frame constants, so the words never need clearing.  Every wait is
+// bounded in time; on expiry the timeout flag is raised and the frame is
+// reported invalid.
 #include <algorithm>
 
 #include "aaag_internal.cuh"
@@ -24,167 +32,164 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
-constexpr int kScanChunk = kScanThreads * kScanItems;
+constexpr int kOffItems = 8;                        // Gaussians per thread in kernel A
+constexpr int kOffTile = kThreads * kOffItems;      // 2048
+constexpr int kChunkTile = kWarps * 32;             // 256 chunks per tile of kernel B
 
-__device__ __forceinline__ int64_t device_count(const uint32_t* n_dev, int64_t n_max) {
-  return n_dev ? min((int64_t)*n_dev, n_max) : n_max;
+constexpr unsigned long long kLbAggregate = 1ull << 38;
+constexpr unsigned long long kLbInclusive = 2ull << 38;
+constexpr unsigned long long kLbValue = (1ull << 38) - 1ull;
+constexpr long long kWaitCycles = 2000000000ll;     // ~1 s at 2 GHz
+
+__device__ __forceinline__ unsigned long long lb_tag(unsigned long long epoch) {
+  return (epoch & 0xffffffull) << 40;
 }
 
-template <bool POPC>
-__device__ __forceinline__ uint32_t scan_input(const uint32_t* in, int64_t i) {
-  const uint32_t v = in[i];
-  return POPC ? (uint32_t)__popc(v) : v;
-}
-
-// ---- exclusive scan over a device-sized array: block sums, scan of the
-// block sums (one block), downsweep.  Blocks loop over 4096-element pieces.
-
-template <bool POPC>
-__global__ void __launch_bounds__(kScanThreads)
-scan_reduce_kernel(const uint32_t* __restrict__ in, const uint32_t* __restrict__ n_dev, int64_t n_max,
-                   unsigned long long* __restrict__ partials) {
-  const int64_t n = device_count(n_dev, n_max);
-  const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
-  __shared__ unsigned long long ws[kScanThreads / 32];
-  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    const int64_t base = b * kScanChunk;
-    unsigned long long s = 0;
+// Warp-parallel decoupled look-back for tile `tile` (> 0), run by one full
+// warp: lanes read the words of 32 predecessors at once and consume them
+// nearest first, up to the first inclusive prefix; a word not yet published
+// stops the window there and is polled again.  Returns the exclusive prefix.
+__device__ __forceinline__ unsigned long long warp_lookback(const volatile unsigned long long* lb, int64_t tile,
+                                                            unsigned long long tag,
+                                                            unsigned long long* timeout_flag) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long prefix = 0;
+  int64_t next = tile - 1;   // nearest predecessor not yet consumed
+  const long long t0 = clock64();
+  for (;;) {
+    const int64_t idx = next - lane;
+    const unsigned long long w = idx >= 0 ? lb[idx] : (tag | kLbInclusive);
+    const bool ready = (w & ~((1ull << 40) - 1ull)) == tag && (w & (3ull << 38)) != 0;
+    const bool incl = ready && (w & kLbInclusive);
+    const unsigned ready_m = __ballot_sync(0xffffffffu, ready);
+    const unsigned incl_m = __ballot_sync(0xffffffffu, incl);
+    const int first_wait = ready_m == 0xffffffffu ? 32 : __ffs(~ready_m) - 1;
+    const int first_incl = incl_m ? __ffs(incl_m) - 1 : 32;
+    const bool done = first_incl < first_wait;
+    const int take = done ? first_incl + 1 : first_wait;
+    unsigned long long v = lane < take ? (w & kLbValue) : 0ull;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-      const int64_t i = base + j * kScanThreads + threadIdx.x;
-      if (i < n) s += scan_input<POPC>(in, i);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long t = 0;
-      for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
-      partials[b] = t;
-    }
-    __syncthreads();
-  }
-}
-
-// single block: exclusive scan of the block partials; the total goes to
-// stats[total_slot]; the total clipped to `cap` goes to *clipped (uint32), and
-// exceeding `cap` raises the overflow flag.
-__global__ void __launch_bounds__(1024)
-scan_partials_kernel(unsigned long long* __restrict__ partials, const uint32_t* __restrict__ n_dev,
-                     int64_t n_max, int64_t cap, unsigned long long* __restrict__ stats, int total_slot,
-                     uint32_t* __restrict__ clipped) {
-  const int64_t n = device_count(n_dev, n_max);
-  const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
-  __shared__ unsigned long long wsum[32];
-  __shared__ unsigned long long carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t b0 = 0; b0 < nb; b0 += 1024) {
-    const int64_t b = b0 + threadIdx.x;
-    const unsigned long long v = b < nb ? partials[b] : 0ull;
-    unsigned long long x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      unsigned long long w = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    prefix += v;
+    if (done) return prefix;
+    next -= take;
+    if (take == 0) {
+      if (clock64() - t0 > kWaitCycles) {
+        if (lane == 0) atomicExch(timeout_flag, 1ull);
+        return prefix;
       }
-      wsum[lane] = w;
+      __nanosleep(32);
     }
-    __syncthreads();
-    const unsigned long long incl = x + (warp > 0 ? wsum[warp - 1] : 0ull) + carry;
-    if (b < nb) partials[b] = incl - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = incl;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    stats[total_slot] = carry;
-    if (carry > (unsigned long long)cap) stats[kStatOverflow] = 1ull;
-    *clipped = (uint32_t)(carry < (unsigned long long)cap ? carry : (unsigned long long)cap);
   }
 }
 
-template <bool POPC>
-__global__ void __launch_bounds__(kScanThreads)
-scan_down_kernel(const uint32_t* __restrict__ in, const uint32_t* __restrict__ n_dev, int64_t n_max,
-                 const unsigned long long* __restrict__ partials, uint32_t* __restrict__ out) {
-  const int64_t n = device_count(n_dev, n_max);
-  const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
-  __shared__ unsigned long long wsum[kScanThreads / 32];
+// exclusive scan of one value per thread over the block; returns the block
+// total in *total (all threads)
+__device__ __forceinline__ unsigned long long block_scan(unsigned long long v, unsigned long long* wsum,
+                                                         unsigned long long* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    // each thread owns kScanItems consecutive elements
-    const int64_t base = b * kScanChunk + (int64_t)threadIdx.x * kScanItems;
-    uint32_t c[kScanItems];
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  unsigned long long pre = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const unsigned long long s = wsum[w];
+    pre += w < warp ? s : 0ull;
+    tot += s;
+  }
+  __syncthreads();
+  *total = tot;
+  return pre + x - v;
+}
+
+// ---- A: chunk offsets and owners
+__global__ void __launch_bounds__(kThreads)
+chunk_offsets_kernel(const uint32_t* __restrict__ counts, int64_t n, int64_t chunk_cap,
+                     uint32_t* __restrict__ offsets, uint32_t* __restrict__ owner,
+                     unsigned long long* __restrict__ lookback, unsigned long long* __restrict__ stats,
+                     uint32_t* __restrict__ n_chunks_clipped) {
+  __shared__ unsigned long long s_wsum[kWarps];
+  __shared__ unsigned long long s_prefix;
+  __shared__ int64_t s_tile;
+  const unsigned long long tag = lb_tag(stats[kStatFrameEpoch]);
+  uint32_t* counter = reinterpret_cast<uint32_t*>(stats + kStatCullTileA);
+  const int64_t n_tiles = (n + kOffTile - 1) / kOffTile;
+  volatile unsigned long long* lb = lookback;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= n_tiles) break;
+    const int64_t base = tile * kOffTile + (int64_t)threadIdx.x * kOffItems;
+    uint32_t c[kOffItems];
     unsigned long long s = 0;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-      c[j] = base + j < n ? scan_input<POPC>(in, base + j) : 0u;
+    for (int j = 0; j < kOffItems; ++j) {
+      c[j] = base + j < n ? counts[base + j] : 0u;
       s += c[j];
     }
-    unsigned long long x = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+    unsigned long long total;
+    const unsigned long long pre = block_scan(s, s_wsum, &total);
+    if (threadIdx.x < 32) {
+      unsigned long long p = 0;
+      if (tile == 0) {
+        if (threadIdx.x == 0) lb[0] = tag | kLbInclusive | (total & kLbValue);
+      } else {
+        if (threadIdx.x == 0) lb[tile] = tag | kLbAggregate | (total & kLbValue);
+        p = warp_lookback(lb, tile, tag, stats + kStatTimeout);
+        if (threadIdx.x == 0) lb[tile] = tag | kLbInclusive | ((p + total) & kLbValue);
+      }
+      if (threadIdx.x == 0) {
+        s_prefix = p;
+        if (tile == n_tiles - 1) {
+          const unsigned long long all = p + total;
+          stats[kStatChunks] = all;
+          if (all > (unsigned long long)chunk_cap) stats[kStatOverflow] = 1ull;
+          *n_chunks_clipped = (uint32_t)(all < (unsigned long long)chunk_cap ? all : (unsigned long long)chunk_cap);
+        }
+      }
     }
-    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    unsigned long long pre = partials[b] + x - s;
-    for (int w = 0; w < warp; ++w) pre += wsum[w];
+    unsigned long long off = s_prefix + pre;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-      if (base + j < n) out[base + j] = pre > 0xffffffffull ? 0xffffffffu : (uint32_t)pre;
-      pre += c[j];
+    for (int j = 0; j < kOffItems; ++j) {
+      const int64_t g = base + j;
+      if (g < n) {
+        offsets[g] = off > 0xffffffffull ? 0xffffffffu : (uint32_t)off;
+        for (uint32_t k = 0; k < c[j] && off + k < (unsigned long long)chunk_cap; ++k) owner[off + k] = (uint32_t)g;
+      }
+      off += c[j];
     }
     __syncthreads();
   }
 }
 
-// ---- chunk ownership
+// ---- B: tile tests, pair offsets and emission
 
-__global__ void __launch_bounds__(kThreads)
-expand_chunks_kernel(const uint32_t* __restrict__ chunk_counts, const uint32_t* __restrict__ chunk_offsets,
-                     int64_t n, int64_t chunk_cap, uint32_t* __restrict__ owner) {
-  for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < n; g += (int64_t)gridDim.x * kThreads) {
-    const uint32_t c = chunk_counts[g];
-    const uint64_t off = chunk_offsets[g];
-    for (uint32_t j = 0; j < c && off + j < (uint64_t)chunk_cap; ++j) owner[off + j] = (uint32_t)g;
+// Is tile (tx, ty) needed by the Gaussian with rows t1..t3 and signed tau
+// (min rho^2 over the tile frustum below tau, Eq. 18)?
+__device__ __forceinline__ bool tile_needed(float4 t1, float4 t2, float4 t3, float tau_signed,
+                                            const FrameConst& fc, int tx, int ty) {
+  const float tau = inflate_tau(fabsf(tau_signed));
+  const float xlo = (float)(tx * kTile), ylo = (float)(ty * kTile);
+  const float xhi = xlo + kTile, yhi = ylo + kTile;
+  if (tau_signed < 0.0f) {
+    // the front of the ellipsoid reaches z_near: frustum truncated there
+    return frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, xlo, xhi, ylo, yhi, tau);
   }
+  ConicTester ct;
+  ct.init(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, tau);
+  return ct.hit(xlo, ylo, xhi, yhi);
 }
 
-struct ChunkGeom {
-  int64_t g;
-  uint4 a;
-  int tx0, ty0, nx, total, local;   // local: chunk index inside the Gaussian
-};
-
-__device__ __forceinline__ ChunkGeom chunk_geom(int64_t c, const uint32_t* owner, const uint32_t* chunk_offsets,
-                                                const uint4* aux) {
-  ChunkGeom q;
-  q.g = owner[c];
-  q.a = aux[q.g];
-  int tx1, ty1;
-  unpack_rect(q.a, q.tx0, q.ty0, tx1, ty1);
-  q.nx = tx1 - q.tx0 + 1;
-  q.total = q.nx * (ty1 - q.ty0 + 1);
-  q.local = (int)(c - (int64_t)chunk_offsets[q.g]);
-  return q;
-}
-
+// One warp per chunk (grid-stride), one lane per tile: the warp ballot of the
+// chunk's needed tiles is stored.
 __global__ void __launch_bounds__(kThreads)
 cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
                  const uint32_t* __restrict__ owner, const uint32_t* __restrict__ chunk_offsets,
@@ -198,28 +203,21 @@ cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
   const bool cull = !(fc.flags & AAAG_FLAG_NO_CULL);
   unsigned long long tested = 0;
   for (int64_t c = warp0; c < nch; c += nwarps) {
-    const ChunkGeom q = chunk_geom(c, owner, chunk_offsets, aux);
-    const int j = q.local * 32 + lane;
+    const uint32_t g = owner[c];
+    const uint4 a = aux[g];
+    const int local = (int)(c - (int64_t)chunk_offsets[g]);
+    int tx0, ty0, tx1, ty1;
+    unpack_rect(a, tx0, ty0, tx1, ty1);
+    const int nx = tx1 - tx0 + 1, total = nx * (ty1 - ty0 + 1);
+    const int j = local * 32 + lane;
     bool keep = false;
-    if (j < q.total) {
-      const int tx = q.tx0 + j % q.nx, ty = q.ty0 + j / q.nx;
-      if (!cull) {
-        keep = true;
+    if (j < total) {
+      if (cull) {
+        const float4* r = reinterpret_cast<const float4*>(rec + g);
+        keep = tile_needed(__ldg(r + 0), __ldg(r + 1), __ldg(r + 2), __uint_as_float(a.z), fc, tx0 + j % nx,
+                           ty0 + j / nx);
       } else {
-        const float4* r = reinterpret_cast<const float4*>(rec + q.g);
-        const float4 t1 = __ldg(r + 0), t2 = __ldg(r + 1), t3 = __ldg(r + 2);
-        const float tau_signed = __uint_as_float(q.a.z);
-        const float tau = inflate_tau(fabsf(tau_signed));
-        const float xlo = (float)(tx * kTile), ylo = (float)(ty * kTile);
-        const float xhi = xlo + kTile, yhi = ylo + kTile;
-        if (tau_signed < 0.0f) {
-          // the front of the ellipsoid reaches z_near: frustum truncated there
-          keep = frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, xlo, xhi, ylo, yhi, tau);
-        } else {
-          ConicTester ct;
-          ct.init(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, tau);
-          keep = ct.hit(xlo, ylo, xhi, yhi);
-        }
+        keep = true;
       }
       ++tested;
     }
@@ -231,87 +229,157 @@ cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
   if (lane == 0 && tested) atomicAdd(&stats[kStatTilesTested], tested);
 }
 
+// Tiles of 256 chunks (8 warps x 32): the tile's pair count is resolved into
+// its global pair offset by look-back, then each warp writes the pairs of its
+// 32 chunks in chunk order (lane i first loads the geometry of chunk i).
 __global__ void __launch_bounds__(kThreads)
-cull_emit_kernel(const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp, const uint32_t* __restrict__ owner,
-                 const uint32_t* __restrict__ chunk_offsets, const uint32_t* __restrict__ n_chunks_dev,
-                 int64_t chunk_cap, const uint32_t* __restrict__ masks, const uint32_t* __restrict__ pair_offsets,
-                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity) {
+cull_emit_kernel(const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
+                 const uint32_t* __restrict__ owner, const uint32_t* __restrict__ chunk_offsets,
+                 const uint32_t* __restrict__ n_chunks_dev, int64_t chunk_cap, const uint32_t* __restrict__ masks,
+                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity,
+                 unsigned long long* __restrict__ lookback, unsigned long long* __restrict__ stats,
+                 uint32_t* __restrict__ n_pairs_clipped) {
+  __shared__ uint32_t s_wcount[kWarps];
+  __shared__ unsigned long long s_prefix;
+  __shared__ int64_t s_tile;
   const FrameConst fc = *fcp;
+  const unsigned long long tag = lb_tag(stats[kStatFrameEpoch]);
+  uint32_t* counter = reinterpret_cast<uint32_t*>(stats + kStatCullTileB);
   const int64_t nch = min((int64_t)*n_chunks_dev, chunk_cap);
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const int64_t n_tiles = (nch + kChunkTile - 1) / kChunkTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  for (int64_t c = warp0; c < nch; c += nwarps) {
-    const uint32_t m = masks[c];
-    if (!(m >> lane & 1u)) continue;
-    const ChunkGeom q = chunk_geom(c, owner, chunk_offsets, aux);
-    const int j = q.local * 32 + lane;
-    const int tx = q.tx0 + j % q.nx, ty = q.ty0 + j / q.nx;
-    const uint64_t p = (uint64_t)pair_offsets[c] + __popc(m & lt);
-    if (p < (uint64_t)capacity) {
-      const uint32_t tile = (uint32_t)(ty * fc.tiles_x + tx);
-      keys[p] = (tile << fc.depth_bits) | q.a.w;
-      vals[p] = (uint32_t)q.g;
+  volatile unsigned long long* lb = lookback;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= n_tiles) break;
+    // lane `lane` of warp `warp` owns chunk c0 + lane
+    const int64_t c0 = tile * kChunkTile + warp * 32;
+    const int64_t c = c0 + lane;
+    uint32_t m = 0u, g = 0u;
+    uint4 a = make_uint4(0u, 0u, 0u, 0u);
+    int local = 0;
+    if (c < nch) {
+      m = masks[c];
+      if (m) {
+        g = owner[c];
+        a = aux[g];
+        local = (int)(c - (int64_t)chunk_offsets[g]);
+      }
     }
+    const uint32_t cnt = (uint32_t)__popc(m);
+    // inclusive scan of the chunk counts inside the warp
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_wcount[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t wc = lane < kWarps ? s_wcount[lane] : 0u;
+      unsigned long long total = wc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+      unsigned long long p = 0;
+      if (tile == 0) {
+        if (lane == 0) lb[0] = tag | kLbInclusive | (total & kLbValue);
+      } else {
+        if (lane == 0) lb[tile] = tag | kLbAggregate | (total & kLbValue);
+        p = warp_lookback(lb, tile, tag, stats + kStatTimeout);
+        if (lane == 0) lb[tile] = tag | kLbInclusive | ((p + total) & kLbValue);
+      }
+      if (lane == 0) {
+        s_prefix = p;
+        if (tile == n_tiles - 1) {
+          const unsigned long long all = p + total;
+          stats[kStatPairs] = all;
+          if (all > (unsigned long long)capacity) stats[kStatOverflow] = 1ull;
+          *n_pairs_clipped = (uint32_t)(all < (unsigned long long)capacity ? all : (unsigned long long)capacity);
+        }
+      }
+    }
+    __syncthreads();
+    unsigned long long wbase = s_prefix;
+    for (int w = 0; w < warp; ++w) wbase += s_wcount[w];
+    // the warp writes its chunks one after the other, one lane per pair
+    unsigned pending = __ballot_sync(0xffffffffu, m != 0u);
+    while (pending) {
+      const int i = __ffs(pending) - 1;
+      pending &= pending - 1u;
+      const uint32_t mi = __shfl_sync(0xffffffffu, m, i);
+      const uint32_t gi = __shfl_sync(0xffffffffu, g, i);
+      const uint32_t ax = __shfl_sync(0xffffffffu, a.x, i), ay = __shfl_sync(0xffffffffu, a.y, i);
+      const uint32_t aw = __shfl_sync(0xffffffffu, a.w, i);
+      const int li = __shfl_sync(0xffffffffu, local, i);
+      const uint32_t before = __shfl_sync(0xffffffffu, incl - cnt, i);
+      if ((mi >> lane) & 1u) {
+        int tx0, ty0, tx1, ty1;
+        unpack_rect(make_uint4(ax, ay, 0u, 0u), tx0, ty0, tx1, ty1);
+        const int nx = tx1 - tx0 + 1;
+        const int j = li * 32 + lane;
+        const uint64_t at = wbase + before + (uint64_t)__popc(mi & lt);
+        if (at < (uint64_t)capacity) {
+          const uint32_t t = (uint32_t)((ty0 + j / nx) * fc.tiles_x + tx0 + j % nx);
+          keys[at] = (t << fc.depth_bits) | aw;
+          vals[at] = gi;
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
 int g_sms = 0;
-int sm_count() {
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms < 1) g_sms = 1;
-  }
-  return g_sms;
-}
+int g_blocks_a = 0, g_blocks_b = 0;
 
-template <bool POPC>
-aaag_status scan(const uint32_t* in, const uint32_t* n_dev, int64_t n_max, int64_t cap, uint32_t* out,
-                 unsigned long long* partials, unsigned long long* stats, int total_slot, uint32_t* clipped,
-                 cudaStream_t st) {
-  const int64_t nb = std::max<int64_t>((n_max + kScanChunk - 1) / kScanChunk, 1);
-  const unsigned grid = (unsigned)std::min<int64_t>(nb, (int64_t)sm_count() * 8);
-  scan_reduce_kernel<POPC><<<grid, kScanThreads, 0, st>>>(in, n_dev, n_max, partials);
-  scan_partials_kernel<<<1, 1024, 0, st>>>(partials, n_dev, n_max, cap, stats, total_slot, clipped);
-  scan_down_kernel<POPC><<<grid, kScanThreads, 0, st>>>(in, n_dev, n_max, partials, out);
-  return check_launch("scan");
+void init_cull_occupancy() {
+  if (g_sms) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (g_sms < 1) g_sms = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_blocks_a, chunk_offsets_kernel, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_blocks_b, cull_emit_kernel, kThreads, 0);
+  g_blocks_a = std::max(1, g_blocks_a);
+  g_blocks_b = std::max(1, g_blocks_b);
 }
 
 }  // namespace
 
+void prepare_cull_kernels() { init_cull_occupancy(); }
+
+int64_t cull_lookback_words(int64_t n, int64_t chunk_cap) {
+  return (n + kOffTile - 1) / kOffTile + (chunk_cap + kChunkTile - 1) / kChunkTile + 2;
+}
+
 aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st) {
+  init_cull_occupancy();
   const int64_t n = ws->n;
   uint32_t* n_chunks = reinterpret_cast<uint32_t*>(ws->stats + kStatChunksClipped);
   uint32_t* n_pairs = reinterpret_cast<uint32_t*>(ws->stats + kStatPairsClipped);
-  // 1. chunk offsets per Gaussian
-  aaag_status e = scan<false>(ws->counts, nullptr, n, ws->chunk_capacity, ws->offsets, ws->scan_partials,
-                              ws->stats, kStatChunks, n_chunks, st);
+  unsigned long long* look_a = ws->cull_lookback;
+  unsigned long long* look_b = ws->cull_lookback + (ws->n_max + kOffTile - 1) / kOffTile + 1;
+  const int64_t tiles_a = std::max<int64_t>((n + kOffTile - 1) / kOffTile, 1);
+  const unsigned grid_a = (unsigned)std::min<int64_t>(tiles_a, (int64_t)g_sms * g_blocks_a);
+  chunk_offsets_kernel<<<grid_a, kThreads, 0, st>>>(ws->counts, n, ws->chunk_capacity, ws->offsets,
+                                                    ws->chunk_owner, look_a, ws->stats, n_chunks);
+  aaag_status e = check_launch("chunk_offsets");
   if (e != AAAG_OK) return e;
-  // 2. owners
-  const unsigned gblocks = (unsigned)std::max<int64_t>(std::min<int64_t>((n + kThreads - 1) / kThreads,
-                                                                        (int64_t)sm_count() * 16), 1);
-  expand_chunks_kernel<<<gblocks, kThreads, 0, st>>>(ws->counts, ws->offsets, n, ws->chunk_capacity,
-                                                     ws->chunk_owner);
-  e = check_launch("expand_chunks");
-  if (e != AAAG_OK) return e;
-  // 3. test
-  const unsigned cblocks = (unsigned)std::max<int64_t>(
-      std::min<int64_t>((ws->chunk_capacity + kWarps - 1) / kWarps, (int64_t)sm_count() * 16), 1);
-  cull_test_kernel<<<cblocks, kThreads, 0, st>>>(ws->records, ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets,
-                                                 n_chunks, ws->chunk_capacity, ws->chunk_mask, ws->stats);
+  const unsigned grid_t = (unsigned)std::max<int64_t>(
+      std::min<int64_t>((ws->chunk_capacity + kWarps - 1) / kWarps, (int64_t)g_sms * 16), 1);
+  cull_test_kernel<<<grid_t, kThreads, 0, st>>>(ws->records, ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets,
+                                                n_chunks, ws->chunk_capacity, ws->chunk_mask, ws->stats);
   e = check_launch("cull_test");
   if (e != AAAG_OK) return e;
-  // 4. pair offsets per chunk
-  e = scan<true>(ws->chunk_mask, n_chunks, ws->chunk_capacity, ws->capacity, ws->chunk_pair_offsets,
-                 ws->scan_partials, ws->stats, kStatPairs, n_pairs, st);
-  if (e != AAAG_OK) return e;
-  // 5. emit
-  cull_emit_kernel<<<cblocks, kThreads, 0, st>>>(ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets, n_chunks,
-                                                 ws->chunk_capacity, ws->chunk_mask, ws->chunk_pair_offsets,
-                                                 ws->keys[0], ws->vals[0], ws->capacity);
+  const int64_t tiles_b = std::max<int64_t>((ws->chunk_capacity + kChunkTile - 1) / kChunkTile, 1);
+  const unsigned grid_b = (unsigned)std::min<int64_t>(tiles_b, (int64_t)g_sms * g_blocks_b);
+  cull_emit_kernel<<<grid_b, kThreads, 0, st>>>(ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets, n_chunks,
+                                                ws->chunk_capacity, ws->chunk_mask, ws->keys[0], ws->vals[0],
+                                                ws->capacity, look_b, ws->stats, n_pairs);
   return check_launch("cull_emit");
 }
 
