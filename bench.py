@@ -531,9 +531,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_value = e2e_steps / (e0.elapsed_time(e1) / 1e3) * world
 
-    # set_frame + preprocess test + preprocess; cull: 3 scans + expand + test
-    # + 3 scans + emit; sort: init + histogram + 4 passes + ranges; render
-    launches_per_frame = 3 + 9 + 7 + 1
+    # set_frame + preprocess test + preprocess; cull: offsets + test + emit;
+    # sort: histogram + 4 passes + ranges; render
+    launches_per_frame = 3 + 3 + 6 + 1
     mean = lambda key: float(np.mean([p[key] for p in per_pose]))
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,

@@ -219,7 +219,10 @@ aaag_status aaag_cull(aaag_workspace* ws, cudaStream_t stream);
  * Order': tile-major, front depth minor) by a stable LSD radix sort with
  * 8-bit digits and decoupled look-back (one pass per digit), then the
  * [start, end) range of each tile.  The pair count is read on the device.
- * Errors: CUDA; a look-back wait that gives up sets the timeout flag.
+ * Its counters and look-back epoch are prepared by aaag_cull, so each
+ * aaag_cull allows exactly one aaag_sort.
+ * Errors: INVALID_ARG (no preceding aaag_cull, or a second sort of the same
+ * pairs), CUDA; a look-back wait that gives up sets the timeout flag.
  * ------------------------------------------------------------------------ */
 aaag_status aaag_sort(aaag_workspace* ws, cudaStream_t stream);
 

@@ -126,6 +126,7 @@ struct aaag_workspace {
   aaag::FrameConst fc;            // host copy of the current frame constants
   aaag::FrameConst* fc_dev;       // device copy read by the kernels
   bool have_frame;
+  bool pairs_unsorted;           // aaag_cull emitted pairs that aaag_sort has not consumed
   int sorted_in_alt;             // which buffer holds the sorted pairs
   int64_t n_sort_tiles;
 };
@@ -158,7 +159,7 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
                                 int key_bits, uint32_t* hist, uint32_t* counters,
                                 unsigned long long* lookback, unsigned long long* epoch,
                                 unsigned long long* timeout_flag, int* result_in_alt,
-                                cudaStream_t st);
+                                cudaStream_t st, bool prepared = false);
 size_t radix_sort_scratch(int64_t n_max);
 
 // ---------------------------------------------------------------------------

@@ -363,6 +363,7 @@ aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, 
   if (e != AAAG_OK) return e;
   ws->fc = fc;
   ws->have_frame = true;
+  ws->pairs_unsorted = false;
   ws->sorted_in_alt = 0;
   set_frame_kernel<<<1, 1, 0, stream>>>(ws->fc_dev, fc, ws->stats + kStatFrameEpoch);
   e = check_launch("set_frame");
@@ -378,7 +379,9 @@ aaag_status aaag_cull(aaag_workspace* ws, cudaStream_t stream) {
     set_error("aaag_cull: workspace without a preprocessed frame");
     return AAAG_ERR_INVALID_ARG;
   }
-  return launch_cull(ws, stream);
+  const aaag_status e = launch_cull(ws, stream);
+  ws->pairs_unsorted = e == AAAG_OK;
+  return e;
 }
 
 aaag_status aaag_sort(aaag_workspace* ws, cudaStream_t stream) {
@@ -386,6 +389,12 @@ aaag_status aaag_sort(aaag_workspace* ws, cudaStream_t stream) {
     set_error("aaag_sort: workspace without a preprocessed frame");
     return AAAG_ERR_INVALID_ARG;
   }
+  if (!ws->pairs_unsorted) {
+    // the digit histograms and tile counters of the sort are prepared by the cull
+    set_error("aaag_sort: no culled pairs to sort (one aaag_sort per aaag_cull)");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  ws->pairs_unsorted = false;
   return launch_sort_pairs(ws, stream);
 }
 

@@ -113,10 +113,18 @@ __global__ void __launch_bounds__(kThreads)
 chunk_offsets_kernel(const uint32_t* __restrict__ counts, int64_t n, int64_t chunk_cap,
                      uint32_t* __restrict__ offsets, uint32_t* __restrict__ owner,
                      unsigned long long* __restrict__ lookback, unsigned long long* __restrict__ stats,
-                     uint32_t* __restrict__ n_chunks_clipped) {
+                     uint32_t* __restrict__ n_chunks_clipped, uint32_t* __restrict__ sort_hist,
+                     uint32_t* __restrict__ sort_counters) {
   __shared__ unsigned long long s_wsum[kWarps];
   __shared__ unsigned long long s_prefix;
   __shared__ int64_t s_tile;
+  if (blockIdx.x == 0) {
+    // prepare K3 for this frame's pairs: zeroed digit histograms and pass
+    // counters, and a fresh epoch for its look-back words
+    for (int i = threadIdx.x; i < 4 * 256; i += kThreads) sort_hist[i] = 0u;
+    if (threadIdx.x < 4) sort_counters[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) stats[kStatSortEpoch] += 1ull;
+  }
   const unsigned long long tag = lb_tag(stats[kStatFrameEpoch]);
   uint32_t* counter = reinterpret_cast<uint32_t*>(stats + kStatCullTileA);
   const int64_t n_tiles = (n + kOffTile - 1) / kOffTile;
@@ -366,7 +374,8 @@ aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st) {
   const int64_t tiles_a = std::max<int64_t>((n + kOffTile - 1) / kOffTile, 1);
   const unsigned grid_a = (unsigned)std::min<int64_t>(tiles_a, (int64_t)g_sms * g_blocks_a);
   chunk_offsets_kernel<<<grid_a, kThreads, 0, st>>>(ws->counts, n, ws->chunk_capacity, ws->offsets,
-                                                    ws->chunk_owner, look_a, ws->stats, n_chunks);
+                                                    ws->chunk_owner, look_a, ws->stats, n_chunks, ws->sort_hist,
+                                                    ws->sort_counters);
   aaag_status e = check_launch("chunk_offsets");
   if (e != AAAG_OK) return e;
   const unsigned grid_t = (unsigned)std::max<int64_t>(

@@ -293,7 +293,7 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
                                 int key_bits, uint32_t* hist, uint32_t* counters,
                                 unsigned long long* lookback, unsigned long long* epoch,
                                 unsigned long long* timeout_flag, int* result_in_alt,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool prepared) {
   const int passes = (key_bits + 7) / 8;
   *result_in_alt = passes & 1;
   if (n_max <= 0 || passes == 0) {
@@ -301,7 +301,7 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
     return AAAG_OK;
   }
   init_occupancy();
-  sort_init_kernel<<<1, 256, 0, st>>>(hist, counters, epoch);
+  if (!prepared) sort_init_kernel<<<1, 256, 0, st>>>(hist, counters, epoch);
   const int64_t hblocks = std::min<int64_t>((n_max + 4095) / 4096, (int64_t)g_sm_count * 4);
   sort_histogram_kernel<<<(unsigned)hblocks, 256, 0, st>>>(keys, n_dev, n_max, passes, hist);
   aaag_status e = check_launch("sort_histogram");
@@ -326,9 +326,10 @@ aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st) {
   // device-side pair count, clipped to the capacity by the pair scan of K2
   const uint32_t* n_dev = reinterpret_cast<const uint32_t*>(ws->stats + kStatPairsClipped);
   int alt = 0;
+  // zeroed digit histograms and pass counters and a fresh epoch come from K2
   aaag_status e = radix_sort_device_n(ws->keys[0], ws->vals[0], ws->keys[1], ws->vals[1], n_dev, ws->capacity, 32,
                           ws->sort_hist, ws->sort_counters, ws->sort_lookback,
-                          ws->stats + kStatSortEpoch, ws->stats + kStatTimeout, &alt, st);
+                          ws->stats + kStatSortEpoch, ws->stats + kStatTimeout, &alt, st, true);
   if (e != AAAG_OK) return e;
   ws->sorted_in_alt = alt;
   if (cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * (size_t)ws->n_tiles, st) != cudaSuccess)

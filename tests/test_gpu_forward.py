@@ -180,6 +180,10 @@ def test_sort_is_bit_exact(wl, ci):
     vals = dev_array(ws, v.vals_unsorted, K, np.uint32)
     aaag.aaag_sort(ws.handle, aaag.current_stream())
     torch.cuda.synchronize()
+    # the cull prepares the sort's counters and epoch: one sort per cull
+    with pytest.raises(aaag.AaagError) as e:
+        aaag.aaag_sort(ws.handle, aaag.current_stream())
+    assert e.value.status == aaag.AAAG_ERR_INVALID_ARG
     v = ws.view()
     sk = dev_array(ws, v.keys_sorted, K, np.uint32)
     sv = dev_array(ws, v.vals_sorted, K, np.uint32)
