@@ -86,8 +86,11 @@ def run_serving(args, dev):
         try:
             server.warm(trace)
             t = time.time()
-            lat = server.serve_streams(trace)
+            lat = server.serve_streams(trace, urgent_pixels=640 * 480)
             ours_wall = time.time() - t
+            t = time.time()
+            lat_f = server.serve_streams(trace)
+            fifo_wall = time.time() - t
             t = time.time()
             lat_b = server.serve(trace)
             batch_wall = time.time() - t
@@ -102,7 +105,10 @@ def run_serving(args, dev):
         out["runs"].append({
             "rate_hz": rate, "seconds": seconds, "requests": len(trace), "views": n_views,
             "server": dict(serve.latency_summary(lat, max(ours_wall, seconds), n_views), slots=n_slots,
-                           budget_gb=args.serve_budget_gb, wall_s=ours_wall, mode="per-request pipelines"),
+                           budget_gb=args.serve_budget_gb, wall_s=ours_wall,
+                           mode="per-request pipelines, 640x480 requests on high-priority streams"),
+            "server_no_priority": dict(serve.latency_summary(lat_f, max(fifo_wall, seconds), n_views),
+                                       wall_s=fifo_wall, mode="per-request pipelines"),
             "server_batches": dict(serve.latency_summary(lat_b, max(batch_wall, seconds), n_views),
                                    wall_s=batch_wall, mode="batch barrier, 8 views, 2 in flight"),
             "plain_per_frame": dict(serve.latency_summary(lat_p, max(plain_wall, seconds), n_views),

@@ -20,7 +20,8 @@ aaag_render_batch); this module only schedules.
 * Per-request pipelines (`serve_streams`): requests are admitted in arrival
   order as slots free up and run concurrently without a batch barrier; the
   views of a request (two for stereo) share one persistent render launch and
-  the request completes on its own event.
+  the request completes on its own event.  Small requests may run on
+  high-priority streams so that they overtake the blocks of large ones.
 
 `plain_renderer` is the reference point: requests in arrival order, one at a
 time, each view rendered with aaag_render_frame on one stream.
@@ -44,6 +45,7 @@ class Slot:
     rgb_flat: torch.Tensor
     alpha_flat: torch.Tensor
     graphs: dict = field(default_factory=dict)
+    urgent: torch.cuda.Stream = None     # high-priority stream for small requests
 
     def outputs(self, cam):
         hw = cam.width * cam.height
@@ -68,7 +70,8 @@ class Server:
             ws = aaag.Workspace(n_max, max_width, max_height, pair_capacity, device=device)
             self.slots.append(Slot(ws, torch.cuda.Stream(device=self.device),
                                    torch.empty(3 * max_width * max_height, device=device),
-                                   torch.empty(max_width * max_height, device=device)))
+                                   torch.empty(max_width * max_height, device=device),
+                                   urgent=torch.cuda.Stream(device=self.device, priority=-1)))
         self.render_stream = torch.cuda.Stream(device=self.device)
         self.max_batch_views = max_batch_views
 
@@ -116,17 +119,19 @@ class Server:
         done.record(self.render_stream)
         return done
 
-    def _launch_request(self, req, slots):
+    def _launch_request(self, req, slots, urgent=False):
         """Per-request pipeline: every view's frame graph on its own slot
         stream, then one persistent render over the request's views on the
-        first slot's stream.  Returns the completion event."""
-        for slot, cam in zip(slots, req.cams):
-            aaag.aaag_graph_launch(self._graph(slot, req.scene, cam), aaag.make_camera(cam),
-                                   slot.stream.cuda_stream)
-        lead = slots[0].stream
-        for slot in slots[1:]:
+        first slot's stream.  `urgent` requests run on the slots'
+        high-priority streams, so their blocks are scheduled before those of
+        requests already running.  Returns the completion event."""
+        streams = [s.urgent if urgent else s.stream for s in slots]
+        for slot, cam, st in zip(slots, req.cams, streams):
+            aaag.aaag_graph_launch(self._graph(slot, req.scene, cam), aaag.make_camera(cam), st.cuda_stream)
+        lead = streams[0]
+        for st in streams[1:]:
             ev = torch.cuda.Event()
-            ev.record(slot.stream)
+            ev.record(st)
             lead.wait_event(ev)
         outs = [slot.outputs(cam) for slot, cam in zip(slots, req.cams)]
         aaag.aaag_render_batch([slot.ws.handle for slot in slots], [o[0].data_ptr() for o in outs],
@@ -135,11 +140,14 @@ class Server:
         done.record(lead)
         return done
 
-    def serve_streams(self, requests, capture=None):
+    def serve_streams(self, requests, capture=None, urgent_pixels=None):
         """Continuous per-request pipelines: requests are admitted in arrival
         order as soon as their views fit into free slots (workspace memory),
         run concurrently on their slots' streams, and complete individually.
-        Same return value and `capture` as `serve`."""
+        Requests with at most `urgent_pixels` pixels in all (None: no
+        priorities) run on high-priority streams, so a small request is not
+        held behind the blocks of a large one.  Same return value and
+        `capture` as `serve`."""
         self.max_views_in_flight = 0
         order = sorted(requests, key=lambda r: r.arrival)
         pending = collections.deque()
@@ -168,7 +176,9 @@ class Server:
             while pending and len(free) >= len(pending[0].cams):
                 req = pending.popleft()
                 slots = [free.pop() for _ in req.cams]
-                inflight.append((self._launch_request(req, slots), req, slots))
+                pix = sum(c.width * c.height for c in req.cams)
+                urgent = urgent_pixels is not None and pix <= urgent_pixels
+                inflight.append((self._launch_request(req, slots, urgent), req, slots))
                 self.max_views_in_flight = max(self.max_views_in_flight, len(self.slots) - len(free))
                 progressed = True
             if not progressed:
