@@ -140,21 +140,30 @@ class Server:
         done.record(lead)
         return done
 
-    def serve_streams(self, requests, capture=None, urgent_pixels=None):
-        """Continuous per-request pipelines: requests are admitted in arrival
-        order as soon as their views fit into free slots (workspace memory),
-        run concurrently on their slots' streams, and complete individually.
-        Requests with at most `urgent_pixels` pixels in all (None: no
-        priorities) run on high-priority streams, so a small request is not
-        held behind the blocks of a large one.  Same return value and
-        `capture` as `serve`."""
+    def serve_streams(self, requests, capture=None, urgent_pixels=None, heavy_pixels=None, max_heavy=1):
+        """Continuous per-request pipelines: requests are admitted as soon as
+        their views fit into free slots (workspace memory), run concurrently
+        on their slots' streams, and complete individually.
+          urgent_pixels: requests of at most this many pixels in all run on
+            high-priority streams, so they are not held behind the blocks of
+            larger ones (None: no priorities).
+          heavy_pixels: requests above this many pixels are "heavy": at most
+            `max_heavy` of them are on the GPU at once, in arrival order,
+            while lighter requests behind them are admitted (None: every
+            request in arrival order).  Running heavy requests concurrently
+            stretches each of them; running them one by one while the light
+            ones overtake keeps their latency close to running alone.
+        Same return value and `capture` as `serve`."""
         self.max_views_in_flight = 0
         order = sorted(requests, key=lambda r: r.arrival)
-        pending = collections.deque()
+        pending = []
         free = list(self.slots)
         inflight = []
         lat = {}
         i = 0
+        pixels = lambda r: sum(c.width * c.height for c in r.cams)
+        heavy = lambda r: heavy_pixels is not None and pixels(r) > heavy_pixels
+        n_heavy = 0
         t0 = time.perf_counter()
         while len(lat) < len(order):
             now = time.perf_counter() - t0
@@ -172,13 +181,26 @@ class Server:
                             capture.setdefault(req.rid, []).append((rgb.cpu(), alpha.cpu()))
                     free.extend(slots)
                     inflight.remove(item)
+                    n_heavy -= heavy(req)
                     progressed = True
-            while pending and len(free) >= len(pending[0].cams):
-                req = pending.popleft()
+            # admission in arrival order; a heavy request waiting for its turn
+            # blocks only later heavy ones
+            k = 0
+            heavy_blocked = False
+            while k < len(pending):
+                req = pending[k]
+                is_heavy = heavy(req)
+                if is_heavy and (heavy_blocked or n_heavy >= max_heavy):
+                    heavy_blocked = True
+                    k += 1
+                    continue
+                if len(free) < len(req.cams):
+                    break
+                pending.pop(k)
                 slots = [free.pop() for _ in req.cams]
-                pix = sum(c.width * c.height for c in req.cams)
-                urgent = urgent_pixels is not None and pix <= urgent_pixels
+                urgent = urgent_pixels is not None and pixels(req) <= urgent_pixels
                 inflight.append((self._launch_request(req, slots, urgent), req, slots))
+                n_heavy += is_heavy
                 self.max_views_in_flight = max(self.max_views_in_flight, len(self.slots) - len(free))
                 progressed = True
             if not progressed:

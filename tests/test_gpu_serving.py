@@ -100,16 +100,19 @@ def test_serving_results_same_alone_and_in_mix():
     serve, server, sc, reqs = small_serving_setup()
     try:
         server.warm(reqs)
-        captured, captured_s = {}, {}
+        captured, captured_s, captured_p = {}, {}, {}
         lat = server.serve(reqs, capture=captured)
         assert len(lat) == len(reqs) and all(x > 0 for x in lat)
         lat = server.serve_streams(reqs, capture=captured_s)
+        assert len(lat) == len(reqs) and all(x > 0 for x in lat)
+        # stereo requests one at a time, the others on high-priority streams
+        lat = server.serve_streams(reqs, capture=captured_p, urgent_pixels=320 * 240, heavy_pixels=320 * 240)
         assert len(lat) == len(reqs) and all(x > 0 for x in lat)
         ds = {k: aaag.DeviceScene(v) for k, v in sc.items()}
         ws = aaag.Workspace(60_000, 320, 272, 1 << 21)
         worst = 0.0
         for r in reqs:
-            for cap in (captured, captured_s):
+            for cap in (captured, captured_s, captured_p):
                 for (rgb_mix, a_mix), cam in zip(cap[r.rid], r.cams):
                     rgb_alone, a_alone = single_frame(ds[r.scene].struct(), cam, ws)
                     worst = max(worst, float((rgb_mix - rgb_alone).abs().max()),
@@ -127,7 +130,8 @@ def test_admission_respects_memory_budget():
     try:
         assert len(server.slots) == 2
         server.warm(reqs)
-        for run in (server.serve, server.serve_streams):
+        policy = lambda r: server.serve_streams(r, urgent_pixels=320 * 240, heavy_pixels=320 * 240)
+        for run in (server.serve, server.serve_streams, policy):
             lat = run(reqs)
             assert len(lat) == len(reqs)
             assert server.max_views_in_flight <= len(server.slots)
