@@ -492,7 +492,10 @@ def run_ours(args):
     for k in range(args.steps):
         s = per_pose[(args.warmup + k) % len(poses)]
         V, K = s["n_visible"], s["n_pairs"]
-        pre_bytes.append(scene.n * 48 + V * (192 + 64 + 16) + (scene.n - V) * 16)
+        # every Gaussian: means, log-scales, opacity, v_train read (32 B), chunk
+        # count written (4 B); every visible one: quaternion and SH read
+        # (16 + 192 B), record, aux word and count written (64 + 16 + 4 B)
+        pre_bytes.append(scene.n * 36 + V * (16 + 192 + 64 + 16 + 4))
         sort_bytes.append(K * (8 * 4 * 2 + 4) + K * 8)     # 4 passes r+w of key+val, histogram read, ranges
     pre_gbs = float(np.sum(pre_bytes) / (stage[:, 0].sum() / 1e3) / 1e9)
     sort_gbs = float(np.sum(sort_bytes) / (stage[:, 2].sum() / 1e3) / 1e9)

@@ -142,12 +142,13 @@ typedef struct {
   float* records;        /* [n][16]: rows t1,t2,t3 of T_view = V T (Gaussian
                             space -> view space; t_i = (A_i0,A_i1,A_i2,mu_v,i)),
                             then (r, g, b, o_hat)                            */
-  uint32_t* aux;         /* [n][4]: inclusive pixel ranges whose centres
-                            can see the Gaussian (x0 | y0<<16, x1 | y1<<16;
-                            its tiles are those holding them), tau_rho float
-                            bits (negated when the ellipsoid reaches znear),
-                            depth-key bits; x0 > x1 = not visible            */
-  uint32_t* counts;      /* [n] chunks of 32 candidate tiles per Gaussian    */
+  uint32_t* aux;         /* [n][4], written for visible Gaussians only:
+                            inclusive pixel ranges whose centres can see the
+                            Gaussian (x0 | y0<<16, x1 | y1<<16; its tiles are
+                            those holding them), tau_rho float bits (negated
+                            when the ellipsoid reaches znear), depth-key bits */
+  uint32_t* counts;      /* [n] chunks of 32 candidate tiles per Gaussian;
+                            0 = not visible                                  */
   uint32_t* offsets;     /* [n] exclusive prefix sum of counts               */
   uint32_t* keys_unsorted;   /* [capacity] pair keys as emitted              */
   uint32_t* vals_unsorted;   /* [capacity] Gaussian index per pair           */

@@ -357,7 +357,7 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int deg
 }
 
 __global__ void __launch_bounds__(128)
-preprocess_backward_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const uint4* __restrict__ aux,
+preprocess_backward_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const uint32_t* __restrict__ counts,
                            const float4* __restrict__ grad, float* __restrict__ g_means,
                            float* __restrict__ g_log_scales, float* __restrict__ g_quats,
                            float* __restrict__ g_opacity, float* __restrict__ g_sh) {
@@ -365,9 +365,9 @@ preprocess_backward_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const
   if (i >= s.n) return;
   const FrameConst fc = *fcp;
   const int K = (s.sh_degree + 1) * (s.sh_degree + 1);
-  const uint4 a = aux[i];
+
   float* gsh = g_sh + (size_t)i * K * 3;
-  if ((a.x & 0xffffu) > (a.y & 0xffffu)) {   // not visible: zero gradient
+  if (counts[i] == 0u) {   // not visible (no tile): zero gradient
     for (int j = 0; j < 3; ++j) g_means[3 * i + j] = g_log_scales[3 * i + j] = 0.0f;
     for (int j = 0; j < 4; ++j) g_quats[4 * i + j] = 0.0f;
     g_opacity[i] = 0.0f;
@@ -542,7 +542,7 @@ aaag_status launch_render_backward(const SceneDev& s, aaag_workspace* ws, const 
   aaag_status e = check_launch("render_backward");
   if (e != AAAG_OK || s.n == 0) return e;
   const unsigned blocks = (unsigned)((s.n + 127) / 128);
-  preprocess_backward_kernel<<<blocks, 128, 0, st>>>(s, ws->fc_dev, ws->aux, ws->grad_acc, out->means,
+  preprocess_backward_kernel<<<blocks, 128, 0, st>>>(s, ws->fc_dev, ws->counts, ws->grad_acc, out->means,
                                                      out->log_scales, out->quats, out->opacity_logits, out->sh);
   return check_launch("preprocess_backward");
 }

@@ -162,14 +162,13 @@ struct Basic {
   float opac;
 };
 
-__device__ __forceinline__ Basic load_basic(const SceneDev& s, const FrameConst& fc, int64_t i) {
+__device__ __forceinline__ Basic basic_from(const float* m, const float* l, float logit, float vtrain,
+                                            const FrameConst& fc) {
   Basic b;
-  b.mx = s.means[3 * i + 0];
-  b.my = s.means[3 * i + 1];
-  b.mz = s.means[3 * i + 2];
-  const float lx = s.log_scales[3 * i + 0], ly = s.log_scales[3 * i + 1], lz = s.log_scales[3 * i + 2];
-  const float logit = s.opacity_logits[i];
-  const float vtrain = s.vhat_train[i];
+  b.mx = m[0];
+  b.my = m[1];
+  b.mz = m[2];
+  const float lx = l[0], ly = l[1], lz = l[2];
   // view-space mean
   b.vx = fc.Rv[0] * b.mx + fc.Rv[1] * b.my + fc.Rv[2] * b.mz + fc.tv[0];
   b.vy = fc.Rv[3] * b.mx + fc.Rv[4] * b.my + fc.Rv[5] * b.mz + fc.tv[1];
@@ -191,6 +190,12 @@ __device__ __forceinline__ Basic load_basic(const SceneDev& s, const FrameConst&
   b.hy = b.s2y + kv;
   b.hz = b.s2z + kv;
   return b;
+}
+
+__device__ __forceinline__ Basic load_basic(const SceneDev& s, const FrameConst& fc, int64_t i) {
+  const float m[3] = {s.means[3 * i + 0], s.means[3 * i + 1], s.means[3 * i + 2]};
+  const float l[3] = {s.log_scales[3 * i + 0], s.log_scales[3 * i + 1], s.log_scales[3 * i + 2]};
+  return basic_from(m, l, s.opacity_logits[i], s.vhat_train[i], fc);
 }
 
 // Conservative early test.  The tau-ellipsoid lies inside the sphere of
@@ -365,30 +370,55 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev& s, const FrameCon
   return visible;
 }
 
-// Phase 1, one thread per Gaussian: the early test.  Rejected Gaussians get
-// an empty rectangle; the others are appended to the candidate list (in a
-// large scene only a few percent survive, scattered over the warps, so the
-// full work runs in a second kernel on converged warps).
+// Phase 1: the early test, four consecutive Gaussians per thread (their
+// means, scales, opacities and training frequencies are loaded as float4
+// vectors when the arrays are 16-byte aligned).  Every chunk count is zeroed
+// (phase 2 writes those of visible Gaussians); survivors are appended to the
+// candidate list (in a large scene only a few percent survive, scattered over
+// the warps, so the full work runs in a second kernel on converged warps).
 __global__ void __launch_bounds__(256)
-preprocess_test_kernel(SceneDev s, const FrameConst* __restrict__ fcp, uint4* __restrict__ aux,
-                       uint32_t* __restrict__ chunks, uint32_t* __restrict__ cand,
-                       uint32_t* __restrict__ n_cand) {
+preprocess_test_kernel(SceneDev s, const FrameConst* __restrict__ fcp, uint32_t* __restrict__ chunks,
+                       uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, int vec4) {
   const FrameConst fc = *fcp;
   const int lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool pass = false;
-  if (i < s.n) {
-    pass = may_be_visible(load_basic(s, fc, i), fc);
-    if (!pass) {
-      aux[i] = make_uint4(1u, 0u, 0u, 0u);   // empty rectangle
-      chunks[i] = 0u;
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  unsigned pass = 0u;   // bit j: Gaussian i0 + j survives
+  if (vec4 && i0 + 3 < s.n) {
+    const float4* m4 = reinterpret_cast<const float4*>(s.means + 3 * i0);
+    const float4* l4 = reinterpret_cast<const float4*>(s.log_scales + 3 * i0);
+    const float4 ma = m4[0], mb = m4[1], mc = m4[2], la = l4[0], lb = l4[1], lc = l4[2];
+    const float4 op = *reinterpret_cast<const float4*>(s.opacity_logits + i0);
+    const float4 vt = *reinterpret_cast<const float4*>(s.vhat_train + i0);
+    const float mm[12] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w, mc.x, mc.y, mc.z, mc.w};
+    const float ll[12] = {la.x, la.y, la.z, la.w, lb.x, lb.y, lb.z, lb.w, lc.x, lc.y, lc.z, lc.w};
+    const float oo[4] = {op.x, op.y, op.z, op.w}, vv[4] = {vt.x, vt.y, vt.z, vt.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (may_be_visible(basic_from(mm + 3 * j, ll + 3 * j, oo[j], vv[j], fc), fc)) pass |= 1u << j;
+    *reinterpret_cast<uint4*>(chunks + i0) = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i0 + j;
+      if (i < s.n) {
+        if (may_be_visible(load_basic(s, fc, i), fc)) pass |= 1u << j;
+        chunks[i] = 0u;
+      }
     }
   }
-  const unsigned ball = __ballot_sync(0xffffffffu, pass);
+  // append the survivors: warp scan of the per-thread counts
+  const uint32_t c = (uint32_t)__popc(pass);
+  uint32_t incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
   uint32_t at = 0u;
-  if (lane == 0 && ball) at = atomicAdd(n_cand, (uint32_t)__popc(ball));
-  at = __shfl_sync(0xffffffffu, at, 0);
-  if (pass) cand[at + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
+  if (lane == 0 && total) at = atomicAdd(n_cand, total);
+  at = __shfl_sync(0xffffffffu, at, 0) + incl - c;
+  for (int j = 0; j < 4; ++j)
+    if (pass >> j & 1u) cand[at++] = (uint32_t)(i0 + j);
 }
 
 // Phase 2: full preprocessing of the candidates (grid-stride over the count
@@ -404,11 +434,7 @@ preprocess_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const uint32_t
     bool visible = false;
     if (j < count) {
       const int64_t g = cand[j];
-      visible = preprocess_one(s, fc, g, rec, aux, chunks);
-      if (!visible) {
-        aux[g] = make_uint4(1u, 0u, 0u, 0u);
-        chunks[g] = 0u;
-      }
+      visible = preprocess_one(s, fc, g, rec, aux, chunks);   // count stays 0 when not
     }
     nvis += (uint32_t)__popc(__ballot_sync(0xffffffffu, visible));
   }
@@ -430,9 +456,13 @@ aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_
   }
   const int threads = 256;
   const int64_t blocks = (s.n + threads - 1) / threads;
+  const int64_t tblocks = ((s.n + 3) / 4 + threads - 1) / threads;
   uint32_t* n_cand = reinterpret_cast<uint32_t*>(ws->stats + kStatCandidates);
-  preprocess_test_kernel<<<(unsigned)blocks, threads, 0, st>>>(s, ws->fc_dev, ws->aux, ws->counts,
-                                                               ws->candidates, n_cand);
+  auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0u; };
+  const int vec4 = a16(s.means) && a16(s.log_scales) && a16(s.opacity_logits) && a16(s.vhat_train) &&
+                   a16(ws->counts);
+  preprocess_test_kernel<<<(unsigned)tblocks, threads, 0, st>>>(s, ws->fc_dev, ws->counts, ws->candidates, n_cand,
+                                                                vec4);
   aaag_status e = check_launch("preprocess_test");
   if (e != AAAG_OK) return e;
   const unsigned grid = (unsigned)std::min<int64_t>(blocks, g_pre_blocks);

@@ -23,10 +23,13 @@ def _need_cuda():
 
 
 def gpu_records(ws, n):
+    """Records, aux words and the visibility (chunk count > 0; aux and records
+    are written for visible Gaussians only)."""
     v = ws.view()
     rec = dev_array(ws, v.records, n * 16, np.float32).reshape(n, 16)
     aux = dev_array(ws, v.aux, n * 4, np.uint32).reshape(n, 4)
-    return rec, aux, v
+    vis = dev_array(ws, v.counts, n, np.uint32) > 0
+    return rec, aux, vis
 
 
 def rect_of(aux):
@@ -93,9 +96,9 @@ def test_preprocess_matches_oracle(wl, ci):
     scene, cams = scenes.workload(wl)
     cam = cams[ci]
     ws, _, _, _ = run_frame(scene, cam, stages=("pre",))
-    rec, aux, _ = gpu_records(ws, scene.n)
+    rec, aux, vis = gpu_records(ws, scene.n)
     x0, y0, x1, y1 = rect_of(aux)
-    vis = x0 <= x1
+    assert np.all(x0[vis] <= x1[vis]) and np.all(y0[vis] <= y1[vis])
     prep = O.prepare(scene, cam)
     alive = prep["alive"].numpy()
     uu = (prep["u_cam"] ** 2).sum(-1).numpy()

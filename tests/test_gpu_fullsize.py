@@ -47,3 +47,33 @@ def test_scene1m_sampled_pixels(scene1m, pose):
     assert amb.mean() < TOL_AMBIG * 5
     assert err[~amb].max() <= TOL_ABS
     assert psnr(g, ref.numpy()) >= TOL_PSNR
+
+
+def test_scene1m_graph_launch_matches_per_stage_calls(scene1m):
+    # bench.py times each frame as one launch of the captured frame graph;
+    # the graph replays the same kernels, so the images are bit-identical
+    scene, poses = scene1m
+    ds = aaag.DeviceScene(scene)
+    cam0 = poses[0]
+    ws = aaag.Workspace(scene.n, cam0.width, cam0.height, BENCH_CAPACITY)
+    st = torch.cuda.Stream()
+    rgb_g = torch.empty(3, cam0.height, cam0.width, device="cuda")
+    alpha_g = torch.empty(cam0.height, cam0.width, device="cuda")
+    stages = (aaag.AAAG_STAGE_PREPROCESS | aaag.AAAG_STAGE_CULL | aaag.AAAG_STAGE_SORT |
+              aaag.AAAG_STAGE_RENDER)
+    graph = aaag.aaag_graph_create(ds.struct(), aaag.make_camera(cam0), aaag.make_params(), ws.handle, stages,
+                                   rgb_g.data_ptr(), alpha_g.data_ptr(), st.cuda_stream)
+    try:
+        for pose in (3, 7, 3):
+            cam = poses[pose]
+            aaag.aaag_graph_launch(graph, aaag.make_camera(cam), st.cuda_stream)
+            st.synchronize()
+            sg = aaag.stats(ws)
+            ws2 = aaag.Workspace(scene.n, cam.width, cam.height, BENCH_CAPACITY)
+            rgb_d, alpha_d = aaag.render(ds, cam, ws2)
+            torch.cuda.synchronize()
+            sd = aaag.stats(ws2)
+            assert sg["status"] == "OK" and sg["n_pairs"] == sd["n_pairs"] and sg["blended"] == sd["blended"]
+            assert torch.equal(rgb_g, rgb_d) and torch.equal(alpha_g, alpha_d)
+    finally:
+        aaag.aaag_graph_destroy(graph)
