@@ -297,6 +297,7 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
         }
         if constexpr (CONVERGENT) {
           bl.end_item(k);
+          if (__all_sync(0xffffffffu, bl.done)) break;   // warp-uniform
         } else {
           if (bl.done) break;
         }
