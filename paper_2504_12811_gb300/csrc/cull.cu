@@ -181,15 +181,18 @@ chunk_offsets_kernel(const uint32_t* __restrict__ counts, int64_t n, int64_t chu
 // ---- B: tile tests, pair offsets and emission
 
 // Is tile (tx, ty) needed by the Gaussian with rows t1..t3 and signed tau
-// (min rho^2 over the tile frustum below tau, Eq. 18)?
+// (min rho^2 over the tile frustum below tau, Eq. 18; with the near-plane
+// rule of Sec. 3.3 when tau is negative)?
 __device__ __forceinline__ bool tile_needed(float4 t1, float4 t2, float4 t3, float tau_signed,
                                             const FrameConst& fc, int tx, int ty) {
   const float tau = inflate_tau(fabsf(tau_signed));
   const float xlo = (float)(tx * kTile), ylo = (float)(ty * kTile);
   const float xhi = xlo + kTile, yhi = ylo + kTile;
   if (tau_signed < 0.0f) {
-    // the front of the ellipsoid reaches z_near: frustum truncated there
-    return frustum_hit<true>(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, xlo, xhi, ylo, yhi, tau);
+    // the front of the ellipsoid reaches z_near
+    NearTester nt;
+    nt.init(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, fc.znear, tau);
+    return nt.hit(xlo, ylo, xhi, yhi);
   }
   ConicTester ct;
   ct.init(t1, t2, t3, fc.fx, fc.fy, fc.cx, fc.cy, tau);

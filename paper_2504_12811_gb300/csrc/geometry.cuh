@@ -205,6 +205,152 @@ struct ConicTester {
   }
 };
 
+// Tile test for a Gaussian whose tau-ellipsoid reaches in front of z_near.
+// A pixel receives such a Gaussian only where rho^2 <= tau and the depth t*
+// of the maximum is not closer than the near plane (Sec. 3.3).  On the ray
+// of screen point (x, y) the maximum is the foot u* = (d x num) / |d|^2 of
+// the perpendicular from the mean (origin of normalised space), so
+// t* = T3.u* + t3.w and, multiplying through by |d|^2 > 0,
+//     F(x, y) = |num|^2 - tau |d|^2 <= 0   and
+//     G(x, y) = (t3.w - z_near) |d|^2 + T3.(d x num) >= 0,
+// both quadratic in (x, y).  A rectangle meets that set iff
+//   (a) it holds one of two interior witnesses: the projected mean (rho = 0,
+//       t* = t3.w) when t3.w >= z_near, or the screen point of smallest rho
+//       on the curve t* = z_near.  The feet u* of all rays from the camera c
+//       lie on the sphere with diameter [0, c], so that curve is the circle
+//       where this sphere meets the plane z = z_near, and rho^2 = |u*|^2 has
+//       a single local minimum on it.  A part of the set lying inside the
+//       rectangle without touching its edges attains its smallest rho either
+//       at the projected mean or at that circle point; or
+//   (b) max(F, -G) <= 0 somewhere on one of its edges.  Along an edge both
+//       are quadratics in the edge parameter, and the minimum of their
+//       maximum lies at an end, at the vertex of F or of G, or where
+//       F + G = 0.  Every candidate is a point of the edge, so evaluating a
+//       spurious one (a vertex of a concave branch, a clamped root) never
+//       accepts a tile wrongly; they are all evaluated without branches.
+// Tighter than the frustum minimum truncated at z_near (Eq. 18), which also
+// keeps tiles seeing only the cap of the ellipsoid in front of the plane,
+// where every ray's maximum lies closer than z_near.  z_near is lowered by
+// 1e-3 relative so that float32 rounding never drops a contributing tile.
+struct NearTester {
+  float3 Nx, Ny, Dx, Dy;   // d num/dx, d num/dy, d d/dx, d d/dy
+  float3 T3, Px, Py, Qx, Qy;
+  float4 t1, t2, t3;
+  float fx, fy, cx, cy, tau, zr, fax, fay, gax, gay;
+  float mx, my, wx, wy;    // witnesses; NaN when absent
+
+  __device__ __forceinline__ void init(float4 t1_, float4 t2_, float4 t3_, float fx_, float fy_, float cx_,
+                                       float cy_, float znear, float tau_) {
+    t1 = t1_;
+    t2 = t2_;
+    t3 = t3_;
+    fx = fx_;
+    fy = fy_;
+    cx = cx_;
+    cy = cy_;
+    tau = tau_;
+    const float zn = znear * (1.0f - 1e-3f);
+    T3 = f3(t3.x, t3.y, t3.z);
+    const float3 Uv = f3(fx * t1.x + cx * t3.x, fx * t1.y + cx * t3.y, fx * t1.z + cx * t3.z);
+    const float Uw = fx * t1.w + cx * t3.w;
+    const float3 Wv = f3(fy * t2.x + cy * t3.x, fy * t2.y + cy * t3.y, fy * t2.z + cy * t3.z);
+    const float Ww = fy * t2.w + cy * t3.w;
+    Nx = Ww * T3 - t3.w * Wv;
+    Ny = t3.w * Uv - Uw * T3;
+    Dx = cross3(Wv, T3);
+    Dy = cross3(T3, Uv);
+    zr = t3.w - zn;
+    fax = dot3(Nx, Nx) - tau * dot3(Dx, Dx);
+    fay = dot3(Ny, Ny) - tau * dot3(Dy, Dy);
+    // G along an edge with num' = E_n, d' = E_d: quadratic coefficient
+    // zr |E_d|^2 + T3.(E_d x E_n); linear terms use P = E_n x T3, Q = T3 x E_d
+    gax = zr * dot3(Dx, Dx) + dot3(T3, cross3(Dx, Nx));
+    gay = zr * dot3(Dy, Dy) + dot3(T3, cross3(Dy, Ny));
+    Px = cross3(Nx, T3);
+    Qx = cross3(T3, Dx);
+    Py = cross3(Ny, T3);
+    Qy = cross3(T3, Dy);
+    const float nan = __int_as_float(0x7fffffff);
+    // witness 1: the projected mean
+    const bool mean_ok = t3.w >= zn;
+    mx = mean_ok ? fx * t1.w / t3.w + cx : nan;
+    my = mean_ok ? fy * t2.w / t3.w + cy : nan;
+    // witness 2: camera c in normalised space (A c + m = 0, A with rows
+    // t_i.xyz, m = view mean), then the circle point closest to the origin
+    const float3 a1 = f3(t1.x, t1.y, t1.z), a2 = f3(t2.x, t2.y, t2.z);
+    const float3 c23 = cross3(a2, T3), c31 = cross3(T3, a1), c12 = cross3(a1, a2);
+    const float det = dot3(a1, c23);
+    const float3 h = (-0.5f / det) * (t1.w * c23 + t2.w * c31 + t3.w * c12);   // c / 2
+    const float iq = rsqrtf(dot3(T3, T3));
+    const float3 k = iq * T3;
+    const float hk = dot3(h, k);
+    const float dist = hk - (zn - t3.w) * iq;   // sphere centre to the plane
+    const float rc2 = dot3(h, h) - dist * dist;
+    float3 hp = h - hk * k;                      // direction of the circle centre from the origin's foot
+    float hpn = dot3(hp, hp);
+    if (!(hpn > 1e-12f * dot3(h, h))) {
+      // rho constant on the circle: any point of it will do
+      hp = cross3(k, fabsf(k.x) < 0.9f ? f3(1.0f, 0.0f, 0.0f) : f3(0.0f, 1.0f, 0.0f));
+      hpn = dot3(hp, hp);
+    }
+    const float3 w = (h - dist * k) - (sqrtf(fmaxf(rc2, 0.0f)) * rsqrtf(hpn)) * hp;
+    const float wz = dot3(T3, w) + t3.w;
+    const bool w_ok = rc2 >= 0.0f && dot3(w, w) <= tau && wz > 0.0f;
+    wx = w_ok ? fx * (dot3(a1, w) + t1.w) / wz + cx : nan;
+    wy = w_ok ? fy * (dot3(a2, w) + t2.w) / wz + cy : nan;
+  }
+
+  __device__ __forceinline__ float Gc(float3 n, float3 d) const {
+    return fmaf(zr, dot3(d, d), dot3(n, cross3(T3, d)));
+  }
+
+  // Does max(F, -G) <= 0 hold at some point of the edge p + t e, t in
+  // [0, len], with num(p) = n, d(p) = d, F(p) = fc, G(p) = gc?
+  __device__ __forceinline__ bool edge(float3 n, float3 d, float fc, float gc, float3 En, float3 Ed, float3 P,
+                                       float3 Q, float fa, float ga, float len) const {
+    const float ded = dot3(d, Ed);
+    const float fb = dot3(n, En) - tau * ded;
+    const float gb = fmaf(zr, ded, 0.5f * (dot3(d, P) + dot3(n, Q)));
+    const float a = fa + ga, b = fb + gb, c = fc + gc;
+    const float q = -(b + copysignf(sqrtf(fmaxf(fmaf(b, b, -a * c), 0.0f)), b));
+    const float cand[4] = {__fdividef(-fb, fa), __fdividef(-gb, ga), __fdividef(q, a), __fdividef(c, q)};
+    bool hit = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float t = fminf(fmaxf(cand[j], 0.0f), len);
+      const float F = fmaf(fmaf(fa, t, 2.0f * fb), t, fc);
+      const float G = fmaf(fmaf(ga, t, 2.0f * gb), t, gc);
+      hit |= (F <= 0.0f) & (G >= 0.0f);
+    }
+    return hit;
+  }
+
+  __device__ __forceinline__ bool hit(float x0, float y0, float x1, float y1) const {
+    // NaN witnesses fail every comparison
+    if ((mx >= x0) & (mx <= x1) & (my >= y0) & (my <= y1)) return true;
+    if ((wx >= x0) & (wx <= x1) & (wy >= y0) & (wy <= y1)) return true;
+    const float cxm = cx - x0, cym = cy - y0;
+    const float3 Uv = f3(fmaf(cxm, t3.x, fx * t1.x), fmaf(cxm, t3.y, fx * t1.y), fmaf(cxm, t3.z, fx * t1.z));
+    const float Uw = fmaf(cxm, t3.w, fx * t1.w);
+    const float3 Wv = f3(fmaf(cym, t3.x, fy * t2.x), fmaf(cym, t3.y, fy * t2.y), fmaf(cym, t3.z, fy * t2.z));
+    const float Ww = fmaf(cym, t3.w, fy * t2.w);
+    const float w = x1 - x0, h = y1 - y0;
+    const float3 n00 = Uw * Wv - Ww * Uv, d00 = cross3(Uv, Wv);
+    const float3 n10 = n00 + w * Nx, d10 = d00 + w * Dx;
+    const float3 n01 = n00 + h * Ny, d01 = d00 + h * Dy;
+    const float3 n11 = n10 + h * Ny, d11 = d10 + h * Dy;
+    const float f00 = dot3(n00, n00) - tau * dot3(d00, d00), g00 = Gc(n00, d00);
+    const float f10 = dot3(n10, n10) - tau * dot3(d10, d10), g10 = Gc(n10, d10);
+    const float f01 = dot3(n01, n01) - tau * dot3(d01, d01), g01 = Gc(n01, d01);
+    const float f11 = dot3(n11, n11) - tau * dot3(d11, d11), g11 = Gc(n11, d11);
+    if (((f00 <= 0.0f) & (g00 >= 0.0f)) | ((f10 <= 0.0f) & (g10 >= 0.0f)) | ((f01 <= 0.0f) & (g01 >= 0.0f)) |
+        ((f11 <= 0.0f) & (g11 >= 0.0f)))
+      return true;
+    return edge(n00, d00, f00, g00, Ny, Dy, Py, Qy, fay, gay, h) | edge(n10, d10, f10, g10, Ny, Dy, Py, Qy, fay, gay, h) |
+           edge(n00, d00, f00, g00, Nx, Dx, Px, Qx, fax, gax, w) | edge(n01, d01, f01, g01, Nx, Dx, Px, Qx, fax, gax, w);
+  }
+};
+
 // Cutoff used by the conservative geometric tests: tau slightly inflated so
 // that float32 rounding never drops a tile or a Gaussian with alpha >= 1/255.
 __device__ __forceinline__ float inflate_tau(float tau) { return tau * (1.0f + 1e-4f) + 1e-4f; }

@@ -106,6 +106,56 @@ __device__ __forceinline__ bool axis_bounds(float3 Ai, float3 A3, float mi, floa
   return true;
 }
 
+// Screen interval of one axis for a Gaussian whose tau-ellipsoid E reaches in
+// front of z_near, intersected into [p1, p2].  Only E's part beyond the near
+// plane is seen (Sec. 3.3), and the projection of that convex part is
+// bounded, whereas the tangent-plane bounds above grow to the whole screen
+// once E crosses the camera plane.  x/z over E and z >= z_near attains its
+// extremes either on the rim (the disc of E in the plane z = z_near, centre
+// s0 A3, s0 = (z_near - m_z)/|A3|^2, radius^2 tau - s0^2 |A3|^2) or at the
+// contact point of a tangent plane x = s z (a root of
+// (m_i - s m_z)^2 = tau |Ai - s A3|^2, Eq. 14 in tangent form) lying at
+// z >= z_near; the interval spans all such candidates.  Roots are kept as
+// fractions so that the contact depth is computed without the slope itself.
+__device__ __forceinline__ void near_bounds(float3 Ai, float3 A3, float mi, float mz, float tau, float z_lo,
+                                            float z_hi, float f, float c, float znear, float& p1, float& p2) {
+  const float q = dot3(A3, A3), ai3 = dot3(Ai, A3), aii = dot3(Ai, Ai);
+  const float s0 = (znear - mz) / q;
+  const float r2 = fmaxf(fmaf(-s0 * s0, q, tau), 0.0f);
+  const float perp2 = fmaxf(aii - ai3 * ai3 / q, 0.0f);
+  const float xc = fmaf(s0, ai3, mi), ext = sqrtf(r2 * perp2);
+  float lo = (xc - ext) / znear, hi = (xc + ext) / znear;
+  const float3 w = mz * Ai - mi * A3;
+  const float3 cr = cross3(Ai, A3);
+  const float D = tau * (dot3(w, w) - tau * dot3(cr, cr));
+  if (D >= 0.0f) {
+    // a2 s^2 - 2 b s + a0 = 0 with a2 = m_z^2 - tau |A3|^2 = z_lo z_hi
+    const float ei = sqrtf(tau * aii);
+    const float a2 = z_lo * z_hi, a0 = (mi - ei) * (mi + ei);
+    const float b = fmaf(mi, mz, -tau * ai3);
+    const float qq = b + copysignf(sqrtf(D), b);
+    const float num[2] = {qq, a0}, den[2] = {a2, qq};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      // tangent plane (den Ai - num A3).u + (den m_i - num m_z) = 0
+      const float3 n = den[k] * Ai - num[k] * A3;
+      const float h = den[k] * mi - num[k] * mz;
+      const float nn = dot3(n, n);
+      const float zc = mz - h * dot3(A3, n) / nn;
+      if (nn > 0.0f && zc >= znear * (1.0f - 1e-3f)) {
+        const float s = num[k] / den[k];
+        lo = fminf(lo, s);
+        hi = fmaxf(hi, s);
+      }
+    }
+  }
+  float q1 = f * lo + c, q2 = f * hi + c;
+  q1 -= 0.01f + 1e-5f * fabsf(q1);
+  q2 += 0.01f + 1e-5f * fabsf(q2);
+  p1 = fmaxf(p1, q1);
+  p2 = fminf(p2, q2);
+}
+
 // Pixels whose centre (i + 1/2) lies in the screen interval [p1, p2],
 // clamped to the image: the only pixels of this axis that can see the
 // Gaussian.  Returns false when there is none.
@@ -278,17 +328,21 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev& s, const FrameCon
     const float zext = sqrtf(tau_c * dot3(A3, A3));
     const float z_lo = vz - zext, z_hi = vz + zext;
     int ix0 = 1, ix1 = 0, iy0 = 1, iy1 = 0;   // pixel-centre ranges
+    const bool eval2d = (fc.flags & AAAG_FLAG_EVAL_2D) != 0;
     bool ok = !inside && z_hi >= fc.znear;
     if (ok) {
       float px1, px2, py1, py2;
       ok = axis_bounds(A1, A3, vx, vz, tau_c, fc.fx, fc.cx, fc.eps, px1, px2) &&
-           axis_bounds(A2, A3, vy, vz, tau_c, fc.fy, fc.cy, fc.eps, py1, py2) &&
-           pixel_range(px1, px2, fc.W, ix0, ix1) && pixel_range(py1, py2, fc.H, iy0, iy1);
+           axis_bounds(A2, A3, vy, vz, tau_c, fc.fy, fc.cy, fc.eps, py1, py2);
+      if (ok && z_lo < fc.znear && !eval2d) {
+        near_bounds(A1, A3, vx, vz, tau_c, z_lo, z_hi, fc.fx, fc.cx, fc.znear, px1, px2);
+        near_bounds(A2, A3, vy, vz, tau_c, z_lo, z_hi, fc.fy, fc.cy, fc.znear, py1, py2);
+      }
+      ok = ok && pixel_range(px1, px2, fc.W, ix0, ix1) && pixel_range(py1, py2, fc.H, iy0, iy1);
     }
     float4 t1 = make_float4(A[0], A[1], A[2], vx);
     float4 t2 = make_float4(A[3], A[4], A[5], vy);
     float4 t3 = make_float4(A[6], A[7], A[8], vz);
-    const bool eval2d = (fc.flags & AAAG_FLAG_EVAL_2D) != 0;
     if (eval2d) {
       // ablation without 3D evaluation: the record encodes the EWA splat
       ok = vz >= fc.znear && ewa_record(A1, A2, A3, vx, vy, vz, tau_c, fc, t1, t2, t3, ix0, ix1, iy0, iy1);

@@ -48,6 +48,30 @@ def pixel_centre_range(p1, p2, size):
     return lo.astype(np.int64), hi.astype(np.int64)
 
 
+def straddles_near(prep):
+    """Gaussians whose tau-ellipsoid reaches in front of z_near (view depth
+    of the front: mean z - sqrt(tau |A3|^2), A3 the z row of T_view)."""
+    T = prep["T_view"].numpy()
+    tau = np.clip(prep["tau"].numpy(), 0, None)
+    z_lo = T[:, 2, 3] - np.sqrt(tau * (T[:, 2, :3] ** 2).sum(1))
+    return z_lo < prep["view"].znear
+
+
+def near_tile_samples(prep, g, tx, ty, m=17):
+    """Smallest rho^2 over an m x m grid of screen points covering tile
+    (tx, ty) (edges included) among the points whose maximum lies at
+    t* >= znear (inf when none), from the oracle's ray maxima."""
+    s = np.linspace(0.0, 16.0, m)
+    X, Y = np.meshgrid(16 * tx + s, 16 * ty + s)
+    one = {k: (v[[g]] if isinstance(v, torch.Tensor) and v.dim() > 0 and v.shape[0] == prep["tau"].shape[0]
+               else v) for k, v in prep.items()}
+    # ray_maximum takes pixel indices and adds the half-pixel offset
+    rho2, ts = O.ray_maximum(one, X.ravel() - 0.5, Y.ravel() - 0.5)
+    rho2, ts = rho2[:, 0].numpy(), ts[:, 0].numpy()
+    ok = ts >= prep["view"].znear * (1 - 2e-3)
+    return float(rho2[ok].min()) if ok.any() else math.inf
+
+
 def contributing_tiles(prep, cam):
     """{Gaussian: set(tile id)} of tiles holding a pixel that the Gaussian
     contributes to (alpha >= 1/255, t* >= znear), from the oracle."""
@@ -119,10 +143,13 @@ def test_preprocess_matches_oracle(wl, ci):
     np.testing.assert_allclose(rec[vis, 15], oh[vis], rtol=2e-5)
     np.testing.assert_allclose(rec[vis, 12:15], prep["rgb"].numpy()[vis], atol=2e-5)
     # GPU pixel ranges contain the pixel centres inside the oracle's bounds
+    # (Eq. 14-17); for Gaussians reaching in front of z_near the GPU bounds
+    # only the part beyond the near plane, checked by the contribution
+    # extents below
     b = O.view_space_bounds(prep)
     ox0, ox1 = pixel_centre_range(b["x"]["p1"].numpy(), b["x"]["p2"].numpy(), cam.width)
     oy0, oy1 = pixel_centre_range(b["y"]["p1"].numpy(), b["y"]["p2"].numpy(), cam.height)
-    ov = b["valid"].numpy() & (ox0 <= ox1) & (oy0 <= oy1) & vis
+    ov = b["valid"].numpy() & (ox0 <= ox1) & (oy0 <= oy1) & vis & ~straddles_near(prep)
     assert ov.sum() > 0
     assert np.all(x0[ov] <= ox0[ov]) and np.all(x1[ov] >= ox1[ov])
     assert np.all(y0[ov] <= oy0[ov]) and np.all(y1[ov] >= oy1[ov])
@@ -170,6 +197,18 @@ def test_cull_is_conservative_and_tight(wl, ci):
     mins = O.tile_min_rho2(prep, vals.astype(np.int64), tx, ty).numpy()
     loose = mins >= tau[vals] * (1 + 1e-3) + 1e-3
     assert loose.mean() < 1e-3, loose.mean()
+    # near-plane rule (Sec. 3.3): a kept tile of a Gaussian reaching in front
+    # of z_near holds a point with rho^2 <= tau whose maximum lies beyond the
+    # near plane (dense sampling of the tile; a sliver between samples may
+    # escape it)
+    sel = np.nonzero(straddles_near(prep)[vals])[0]
+    if wl == "near":
+        assert sel.size > 100
+    if sel.size:
+        sel = np.random.default_rng(0).choice(sel, size=min(sel.size, 400), replace=False)
+        far = [near_tile_samples(prep, int(vals[i]), int(tx[i]), int(ty[i])) > tau[vals[i]] * (1 + 1e-3) + 1e-3
+               for i in sel]
+        assert np.mean(far) < 2e-2, np.mean(far)
 
 
 @pytest.mark.parametrize("wl,ci", [("small", 0), ("near", 0)])
