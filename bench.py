@@ -489,6 +489,8 @@ def run_ours(args):
     except (OSError, KeyError, ValueError):
         hbm_peak, hbm_src = 6800.0, "fallback"
     pre_bytes, sort_bytes = [], []
+    kv = ws.view()
+    passes = (kv.tile_bits + kv.depth_bits + 7) // 8     # radix passes of the pair keys
     for k in range(args.steps):
         s = per_pose[(args.warmup + k) % len(poses)]
         V, K = s["n_visible"], s["n_pairs"]
@@ -496,7 +498,7 @@ def run_ours(args):
         # count written (4 B); every visible one: quaternion and SH read
         # (16 + 192 B), record, aux word and count written (64 + 16 + 4 B)
         pre_bytes.append(scene.n * 36 + V * (16 + 192 + 64 + 16 + 4))
-        sort_bytes.append(K * (8 * 4 * 2 + 4) + K * 8)     # 4 passes r+w of key+val, histogram read, ranges
+        sort_bytes.append(K * (8 * passes * 2 + 4) + K * 8)   # passes r+w of key+val, histogram read, ranges
     pre_gbs = float(np.sum(pre_bytes) / (stage[:, 0].sum() / 1e3) / 1e9)
     sort_gbs = float(np.sum(sort_bytes) / (stage[:, 2].sum() / 1e3) / 1e9)
 
@@ -548,8 +550,8 @@ def run_ours(args):
     e2e_value = e2e_steps / (e0.elapsed_time(e1) / 1e3) * world
 
     # set_frame + preprocess test + preprocess; cull: offsets + test + emit;
-    # sort: histogram + 4 passes + ranges; render
-    launches_per_frame = 3 + 3 + 6 + 1
+    # sort: histogram + radix passes + ranges; render
+    launches_per_frame = 3 + 3 + (2 + passes) + 1
     mean = lambda key: float(np.mean([p[key] for p in per_pose]))
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,

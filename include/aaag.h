@@ -158,8 +158,11 @@ typedef struct {
   float* final_T;        /* [height][width] transmittance after the last blend */
   uint32_t* n_blended;   /* [height][width] contributors blended             */
   int32_t tiles_x, tiles_y;
-  int32_t tile_bits;     /* key = tile << (32 - tile_bits) | depth key       */
-  int32_t depth_shift;   /* depth key = (bits(z) - bits(znear)) >> shift      */
+  int32_t tile_bits;     /* key = tile << depth_bits | depth key             */
+  int32_t depth_shift;   /* depth key = (bits(z) - bits(znear)) >> shift,
+                            clamped to the largest depth key                 */
+  int32_t depth_bits;    /* tile_bits + depth_bits = 24 when that leaves at
+                            least 16 depth bits (three radix passes), else 32 */
 } aaag_workspace_view;
 
 /* --------------------------------------------------------------------------

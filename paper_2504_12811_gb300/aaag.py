@@ -67,7 +67,8 @@ class aaag_workspace_view(C.Structure):
                 ("offsets", C.c_void_p), ("keys_unsorted", C.c_void_p), ("vals_unsorted", C.c_void_p),
                 ("keys_sorted", C.c_void_p), ("vals_sorted", C.c_void_p), ("tile_ranges", C.c_void_p),
                 ("final_T", C.c_void_p), ("n_blended", C.c_void_p), ("tiles_x", C.c_int32),
-                ("tiles_y", C.c_int32), ("tile_bits", C.c_int32), ("depth_shift", C.c_int32)]
+                ("tiles_y", C.c_int32), ("tile_bits", C.c_int32), ("depth_shift", C.c_int32),
+                ("depth_bits", C.c_int32)]
 
 
 # (name, restype, argtypes) of every exported symbol

@@ -9,6 +9,7 @@
 namespace aaag {
 
 constexpr int kTile = 16;                 // 16x16 pixel tiles
+constexpr int kMinDepthBits = 16;         // depth-key bits below which pair keys grow to 32 bits
 constexpr int kTilePixels = kTile * kTile;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
@@ -43,7 +44,7 @@ struct FrameConst {
   float eps;            // angle clamp epsilon
   uint32_t flags;
   int tile_bits;        // bits of the tile id in a pair key
-  int depth_bits;       // 32 - tile_bits
+  int depth_bits;       // key_bits - tile_bits (key_bits 24 or 32)
   int depth_shift;      // depth key = (bits(z) - bits(znear)) >> depth_shift
   uint32_t znear_bits;
   int sh_degree;

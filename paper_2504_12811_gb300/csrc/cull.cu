@@ -201,7 +201,7 @@ __device__ __forceinline__ bool tile_needed(float4 t1, float4 t2, float4 t3, flo
 
 // One warp per chunk (grid-stride), one lane per tile: the warp ballot of the
 // chunk's needed tiles is stored.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
                  const uint32_t* __restrict__ owner, const uint32_t* __restrict__ chunk_offsets,
                  const uint32_t* __restrict__ n_chunks_dev, int64_t chunk_cap, uint32_t* __restrict__ masks,

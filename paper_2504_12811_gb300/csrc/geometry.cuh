@@ -234,9 +234,8 @@ struct ConicTester {
 // 1e-3 relative so that float32 rounding never drops a contributing tile.
 struct NearTester {
   float3 Nx, Ny, Dx, Dy;   // d num/dx, d num/dy, d d/dx, d d/dy
-  float3 T3, Px, Py, Qx, Qy;
   float4 t1, t2, t3;
-  float fx, fy, cx, cy, tau, zr, fax, fay, gax, gay;
+  float fx, fy, cx, cy, tau, zr;
   float mx, my, wx, wy;    // witnesses; NaN when absent
 
   __device__ __forceinline__ void init(float4 t1_, float4 t2_, float4 t3_, float fx_, float fy_, float cx_,
@@ -250,7 +249,7 @@ struct NearTester {
     cy = cy_;
     tau = tau_;
     const float zn = znear * (1.0f - 1e-3f);
-    T3 = f3(t3.x, t3.y, t3.z);
+    const float3 T3 = f3(t3.x, t3.y, t3.z);
     const float3 Uv = f3(fx * t1.x + cx * t3.x, fx * t1.y + cx * t3.y, fx * t1.z + cx * t3.z);
     const float Uw = fx * t1.w + cx * t3.w;
     const float3 Wv = f3(fy * t2.x + cy * t3.x, fy * t2.y + cy * t3.y, fy * t2.z + cy * t3.z);
@@ -260,16 +259,6 @@ struct NearTester {
     Dx = cross3(Wv, T3);
     Dy = cross3(T3, Uv);
     zr = t3.w - zn;
-    fax = dot3(Nx, Nx) - tau * dot3(Dx, Dx);
-    fay = dot3(Ny, Ny) - tau * dot3(Dy, Dy);
-    // G along an edge with num' = E_n, d' = E_d: quadratic coefficient
-    // zr |E_d|^2 + T3.(E_d x E_n); linear terms use P = E_n x T3, Q = T3 x E_d
-    gax = zr * dot3(Dx, Dx) + dot3(T3, cross3(Dx, Nx));
-    gay = zr * dot3(Dy, Dy) + dot3(T3, cross3(Dy, Ny));
-    Px = cross3(Nx, T3);
-    Qx = cross3(T3, Dx);
-    Py = cross3(Ny, T3);
-    Qy = cross3(T3, Dy);
     const float nan = __int_as_float(0x7fffffff);
     // witness 1: the projected mean
     const bool mean_ok = t3.w >= zn;
@@ -300,17 +289,24 @@ struct NearTester {
     wy = w_ok ? fy * (dot3(a2, w) + t2.w) / wz + cy : nan;
   }
 
-  __device__ __forceinline__ float Gc(float3 n, float3 d) const {
-    return fmaf(zr, dot3(d, d), dot3(n, cross3(T3, d)));
+  __device__ __forceinline__ float3 T3() const { return f3(t3.x, t3.y, t3.z); }
+  __device__ __forceinline__ float F(float3 n, float3 d) const { return dot3(n, n) - tau * dot3(d, d); }
+  __device__ __forceinline__ float G(float3 n, float3 d) const {
+    return fmaf(zr, dot3(d, d), dot3(n, cross3(T3(), d)));
   }
 
   // Does max(F, -G) <= 0 hold at some point of the edge p + t e, t in
-  // [0, len], with num(p) = n, d(p) = d, F(p) = fc, G(p) = gc?
-  __device__ __forceinline__ bool edge(float3 n, float3 d, float fc, float gc, float3 En, float3 Ed, float3 P,
-                                       float3 Q, float fa, float ga, float len) const {
+  // [0, len], with num(p) = n, d(p) = d, F(p) = fc, G(p) = gc, and
+  // num' = En, d' = Ed along it?  F and G are a t^2 + 2 b t + c there, with
+  // G's quadratic coefficient zr |Ed|^2 + T3.(Ed x En).
+  __device__ __forceinline__ bool edge(float3 n, float3 d, float fc, float gc, float3 En, float3 Ed,
+                                       float len) const {
+    const float3 t3v = T3();
     const float ded = dot3(d, Ed);
+    const float fa = F(En, Ed);
+    const float ga = fmaf(zr, dot3(Ed, Ed), dot3(t3v, cross3(Ed, En)));
     const float fb = dot3(n, En) - tau * ded;
-    const float gb = fmaf(zr, ded, 0.5f * (dot3(d, P) + dot3(n, Q)));
+    const float gb = fmaf(zr, ded, 0.5f * (dot3(t3v, cross3(d, En)) + dot3(t3v, cross3(Ed, n))));
     const float a = fa + ga, b = fb + gb, c = fc + gc;
     const float q = -(b + copysignf(sqrtf(fmaxf(fmaf(b, b, -a * c), 0.0f)), b));
     const float cand[4] = {__fdividef(-fb, fa), __fdividef(-gb, ga), __fdividef(q, a), __fdividef(c, q)};
@@ -318,9 +314,9 @@ struct NearTester {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float t = fminf(fmaxf(cand[j], 0.0f), len);
-      const float F = fmaf(fmaf(fa, t, 2.0f * fb), t, fc);
-      const float G = fmaf(fmaf(ga, t, 2.0f * gb), t, gc);
-      hit |= (F <= 0.0f) & (G >= 0.0f);
+      const float Ft = fmaf(fmaf(fa, t, 2.0f * fb), t, fc);
+      const float Gt = fmaf(fmaf(ga, t, 2.0f * gb), t, gc);
+      hit |= (Ft <= 0.0f) & (Gt >= 0.0f);
     }
     return hit;
   }
@@ -335,19 +331,21 @@ struct NearTester {
     const float3 Wv = f3(fmaf(cym, t3.x, fy * t2.x), fmaf(cym, t3.y, fy * t2.y), fmaf(cym, t3.z, fy * t2.z));
     const float Ww = fmaf(cym, t3.w, fy * t2.w);
     const float w = x1 - x0, h = y1 - y0;
+    // corner (x0, y0), then the top and left edges from it
     const float3 n00 = Uw * Wv - Ww * Uv, d00 = cross3(Uv, Wv);
+    const float f00 = F(n00, d00), g00 = G(n00, d00);
+    if ((f00 <= 0.0f) & (g00 >= 0.0f)) return true;
+    if (edge(n00, d00, f00, g00, Nx, Dx, w) || edge(n00, d00, f00, g00, Ny, Dy, h)) return true;
+    // corner (x1, y0) and the right edge
     const float3 n10 = n00 + w * Nx, d10 = d00 + w * Dx;
+    const float f10 = F(n10, d10), g10 = G(n10, d10);
+    if ((f10 <= 0.0f) & (g10 >= 0.0f)) return true;
+    if (edge(n10, d10, f10, g10, Ny, Dy, h)) return true;
+    // corner (x0, y1) and the bottom edge (its far end (x1, y1) is a candidate)
     const float3 n01 = n00 + h * Ny, d01 = d00 + h * Dy;
-    const float3 n11 = n10 + h * Ny, d11 = d10 + h * Dy;
-    const float f00 = dot3(n00, n00) - tau * dot3(d00, d00), g00 = Gc(n00, d00);
-    const float f10 = dot3(n10, n10) - tau * dot3(d10, d10), g10 = Gc(n10, d10);
-    const float f01 = dot3(n01, n01) - tau * dot3(d01, d01), g01 = Gc(n01, d01);
-    const float f11 = dot3(n11, n11) - tau * dot3(d11, d11), g11 = Gc(n11, d11);
-    if (((f00 <= 0.0f) & (g00 >= 0.0f)) | ((f10 <= 0.0f) & (g10 >= 0.0f)) | ((f01 <= 0.0f) & (g01 >= 0.0f)) |
-        ((f11 <= 0.0f) & (g11 >= 0.0f)))
-      return true;
-    return edge(n00, d00, f00, g00, Ny, Dy, Py, Qy, fay, gay, h) | edge(n10, d10, f10, g10, Ny, Dy, Py, Qy, fay, gay, h) |
-           edge(n00, d00, f00, g00, Nx, Dx, Px, Qx, fax, gax, w) | edge(n01, d01, f01, g01, Nx, Dx, Px, Qx, fax, gax, w);
+    const float f01 = F(n01, d01), g01 = G(n01, d01);
+    if ((f01 <= 0.0f) & (g01 >= 0.0f)) return true;
+    return edge(n01, d01, f01, g01, Nx, Dx, w);
   }
 };
 

@@ -327,7 +327,8 @@ aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st) {
   const uint32_t* n_dev = reinterpret_cast<const uint32_t*>(ws->stats + kStatPairsClipped);
   int alt = 0;
   // zeroed digit histograms and pass counters and a fresh epoch come from K2
-  aaag_status e = radix_sort_device_n(ws->keys[0], ws->vals[0], ws->keys[1], ws->vals[1], n_dev, ws->capacity, 32,
+  const int key_bits = ws->fc.tile_bits + ws->fc.depth_bits;
+  aaag_status e = radix_sort_device_n(ws->keys[0], ws->vals[0], ws->keys[1], ws->vals[1], n_dev, ws->capacity, key_bits,
                           ws->sort_hist, ws->sort_counters, ws->sort_lookback,
                           ws->stats + kStatSortEpoch, ws->stats + kStatTimeout, &alt, st, true);
   if (e != AAAG_OK) return e;

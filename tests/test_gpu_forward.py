@@ -173,7 +173,7 @@ def test_cull_is_conservative_and_tight(wl, ci):
     v = ws.view()
     keys = dev_array(ws, v.keys_unsorted, K, np.uint32)
     vals = dev_array(ws, v.vals_unsorted, K, np.uint32)
-    dbits = 32 - v.tile_bits
+    dbits = v.depth_bits
     tiles = keys >> dbits
     # deterministic emission order: Gaussian index, then row-major tile id
     order_key = vals.astype(np.int64) * (1 << 20) + tiles.astype(np.int64)
@@ -235,7 +235,7 @@ def test_sort_is_bit_exact(wl, ci):
     # tile ranges
     ntiles = v.tiles_x * v.tiles_y
     ranges = dev_array(ws, v.tile_ranges, 2 * ntiles, np.uint32).reshape(ntiles, 2)
-    t = sk >> (32 - v.tile_bits)
+    t = sk >> v.depth_bits
     for tile in range(ntiles):
         sel = np.nonzero(t == tile)[0]
         if sel.size:
