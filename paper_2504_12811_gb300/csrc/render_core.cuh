@@ -165,17 +165,21 @@ struct SmemQueue {
   uint32_t used;              // bit s: slot s holds an entry
   float ft;                   // t* of the nearest entry (n > 0)
   __device__ __forceinline__ int slot_at(int i) const { return (int)((order >> (4 * i)) & 15ull); }
-  // blend the nearest entry and remove it
-  template <class Blender>
-  __device__ __forceinline__ void release(Blender& bl) {
+  // remove the nearest entry, returning its alpha and payload
+  __device__ __forceinline__ void pop(float& a, typename Q::Payload& p) {
     const int s = (int)(order & 15ull);
-    float a;
-    typename Q::Payload p;
     q->load(s, tid, a, p);
-    bl.blend(a, p);
     order >>= 4;
     used &= ~(1u << s);
     if (--n > 0) ft = q->t((int)(order & 15ull), tid);
+  }
+  // blend the nearest entry and remove it
+  template <class Blender>
+  __device__ __forceinline__ void release(Blender& bl) {
+    float a;
+    typename Q::Payload p;
+    pop(a, p);
+    bl.blend(a, p);
   }
   // sorted insert (n < kQueue), after every entry with an equal t*
   __device__ __forceinline__ void insert(float t, float a, typename Q::Payload p) {
@@ -198,6 +202,23 @@ struct EvalState {
   float n0, n1, n2, d0, d1, d2, inv, rho2;
 };
 
+// Warp-wide release rounds (convergent traversal): while any lane of the warp
+// wants to release its nearest entry, every such lane pops one and the whole
+// warp calls Blender::release_round, so that lanes releasing the same
+// Gaussian can be combined.  Each lane releases in the same order as with a
+// per-lane loop.
+template <class Q, class Blender, class Want>
+__device__ __forceinline__ void release_rounds(SmemQueue<Q>& q, Blender& bl, Want want) {
+  for (;;) {
+    const bool w = want();
+    if (!__any_sync(0xffffffffu, w)) return;
+    float a = 0.0f;
+    typename Q::Payload p{};
+    if (w) q.pop(a, p);
+    bl.release_round(w, a, p);
+  }
+}
+
 // Traverse one tile for one pixel.  Blender must provide:
 //   using Queue;                                     its queue store
 //   bool done;                                       pixel finished
@@ -206,7 +227,10 @@ struct EvalState {
 //   Queue::Payload payload(int k);                   what a queued entry of k carries
 //   void begin_batch(uint32_t b0, int cnt);          pairs b0 .. b0+cnt-1 are staged
 // With CONVERGENT, every lane runs every iteration (no early exit from the
-// pair loop) and the Blender also provides
+// pair loop), every release is a warp-wide round, and the Blender also
+// provides
+//   void release_round(bool w, float a, Queue::Payload);   warp-converged; lanes
+//                                                    with w blend the popped entry
 //   void end_item(int k);                            warp-converged, after item k
 //   void end_batch(uint32_t b0, int cnt);            block-converged, after a batch
 // The arithmetic, and so every blend decision, is the same either way.
@@ -248,57 +272,113 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
       for (int k = 0; k < cnt; ++k) {
         const float4 bq = s.b[k];
         if (!(__float_as_uint(bq.w) & wbit)) continue;   // warp-uniform
-        if (!bl.done) {
-          ++neval;
-          const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
-          const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
-          const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
-          const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
-          const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
-          const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
-          const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
-          const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
-          const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
-          // rho^2 > tau+ rules out alpha >= 1/255 without a division
-          if (nn <= c.w * dd) {
-            const float inv = __fdividef(1.0f, dd);
-            const float rho2 = nn * inv;
-            const float raw = a.w * __expf(-0.5f * rho2);
-            const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
-            if (raw >= kAlphaMin && ts >= fc.znear) {
-              const float Lnext = by_key ? s.L[k] : -kInf;
-              const float ca = fminf(raw, kAlphaMax);
-              const EvalState ev{k, n0, n1, n2, d0, d1, d2, inv, rho2};
-              // 1. queued entries in front of the new one that nothing later can precede
-              while (q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext) q.release(bl);
-              if (!bl.done) {
-                if (ts < Lnext || !resort) {
-                  // 2. the new contributor, then the rest below L_next
-                  bl.blend_new(ca, ev);
-                  while (q.n > 0 && !bl.done && q.ft < Lnext) q.release(bl);
-                } else {
-                  // 3. queue it; when full, release the nearer of the front and
-                  // the new entry early (a potential misorder)
-                  bool insert = true;
-                  if (q.n == kQueue) {
-                    ++nmis;
-                    if (ts < q.ft) {
-                      bl.blend_new(ca, ev);
-                      insert = false;
-                    } else {
-                      q.release(bl);
+        if constexpr (CONVERGENT) {
+          // the same decisions as below, with the releases taken out of the
+          // per-lane branches into warp-wide rounds
+          bool contrib = false;
+          float ts = 0.0f, ca = 0.0f, Lnext = 0.0f;
+          EvalState ev{k, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          if (!bl.done) {
+            ++neval;
+            const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
+            const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
+            const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
+            const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
+            const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
+            const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
+            const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
+            const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
+            const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+            if (nn <= c.w * dd) {
+              const float inv = __fdividef(1.0f, dd);
+              const float rho2 = nn * inv;
+              const float raw = a.w * __expf(-0.5f * rho2);
+              const float t = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
+              if (raw >= kAlphaMin && t >= fc.znear) {
+                contrib = true;
+                ts = t;
+                ca = fminf(raw, kAlphaMax);
+                Lnext = by_key ? s.L[k] : -kInf;
+                ev = EvalState{k, n0, n1, n2, d0, d1, d2, inv, rho2};
+              }
+            }
+          }
+          // 1. queued entries in front of the new one that nothing later can precede
+          release_rounds(q, bl, [&] { return contrib && q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext; });
+          const bool live = contrib && !bl.done;
+          const bool imm = live && (ts < Lnext || !resort);
+          bool ins = live && !imm;
+          // 2. the new contributor, then the rest below L_next
+          if (imm) bl.blend_new(ca, ev);
+          release_rounds(q, bl, [&] { return imm && q.n > 0 && !bl.done && q.ft < Lnext; });
+          // 3. queue it; when full, release the nearer of the front and the new
+          // entry early (a potential misorder)
+          bool early = false;
+          if (ins && q.n == kQueue) {
+            ++nmis;
+            if (ts < q.ft) {
+              bl.blend_new(ca, ev);
+              ins = false;
+            } else {
+              early = true;
+            }
+          }
+          release_rounds(q, bl, [&] {
+            const bool e = early;
+            early = false;
+            return e;
+          });
+          if (ins && !bl.done) q.insert(ts, ca, bl.payload(k));
+          bl.end_item(k);
+          if (__all_sync(0xffffffffu, bl.done)) break;   // warp-uniform
+        } else {
+          if (!bl.done) {
+            ++neval;
+            const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
+            const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
+            const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
+            const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
+            const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
+            const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
+            const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
+            const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
+            const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+            // rho^2 > tau+ rules out alpha >= 1/255 without a division
+            if (nn <= c.w * dd) {
+              const float inv = __fdividef(1.0f, dd);
+              const float rho2 = nn * inv;
+              const float raw = a.w * __expf(-0.5f * rho2);
+              const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
+              if (raw >= kAlphaMin && ts >= fc.znear) {
+                const float Lnext = by_key ? s.L[k] : -kInf;
+                const float ca = fminf(raw, kAlphaMax);
+                const EvalState ev{k, n0, n1, n2, d0, d1, d2, inv, rho2};
+                // 1. queued entries in front of the new one that nothing later can precede
+                while (q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext) q.release(bl);
+                if (!bl.done) {
+                  if (ts < Lnext || !resort) {
+                    // 2. the new contributor, then the rest below L_next
+                    bl.blend_new(ca, ev);
+                    while (q.n > 0 && !bl.done && q.ft < Lnext) q.release(bl);
+                  } else {
+                    // 3. queue it; when full, release the nearer of the front and
+                    // the new entry early (a potential misorder)
+                    bool insert = true;
+                    if (q.n == kQueue) {
+                      ++nmis;
+                      if (ts < q.ft) {
+                        bl.blend_new(ca, ev);
+                        insert = false;
+                      } else {
+                        q.release(bl);
+                      }
                     }
+                    if (insert && !bl.done) q.insert(ts, ca, bl.payload(k));
                   }
-                  if (insert && !bl.done) q.insert(ts, ca, bl.payload(k));
                 }
               }
             }
           }
-        }
-        if constexpr (CONVERGENT) {
-          bl.end_item(k);
-          if (__all_sync(0xffffffffu, bl.done)) break;   // warp-uniform
-        } else {
           if (bl.done) break;
         }
       }
@@ -306,7 +386,11 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
     if constexpr (CONVERGENT) bl.end_batch(b0, cnt);
     __syncthreads();
   }
-  while (q.n > 0 && !bl.done) q.release(bl);
+  if constexpr (CONVERGENT) {
+    release_rounds(q, bl, [&] { return q.n > 0 && !bl.done; });
+  } else {
+    while (q.n > 0 && !bl.done) q.release(bl);
+  }
 }
 
 }  // namespace aaag
