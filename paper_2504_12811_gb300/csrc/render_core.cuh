@@ -308,11 +308,11 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
           const bool live = contrib && !bl.done;
           const bool imm = live && (ts < Lnext || !resort);
           bool ins = live && !imm;
-          // 2. the new contributor, then the rest below L_next
+          // 2. the new contributor, then the rest below L_next; 3. queue it,
+          // and when the queue is full release the nearer of the front and the
+          // new entry early (a potential misorder).  The lanes of 2 and 3 are
+          // disjoint, so their releases share rounds.
           if (imm) bl.blend_new(ca, ev);
-          release_rounds(q, bl, [&] { return imm && q.n > 0 && !bl.done && q.ft < Lnext; });
-          // 3. queue it; when full, release the nearer of the front and the new
-          // entry early (a potential misorder)
           bool early = false;
           if (ins && q.n == kQueue) {
             ++nmis;
@@ -326,7 +326,7 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
           release_rounds(q, bl, [&] {
             const bool e = early;
             early = false;
-            return e;
+            return e || (imm && q.n > 0 && !bl.done && q.ft < Lnext);
           });
           if (ins && !bl.done) q.insert(ts, ca, bl.payload(k));
           bl.end_item(k);
