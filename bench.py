@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-train", action="store_true", help="skip the 500k-Gaussian training-step timing")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--capacity", type=int, default=48 << 20)
-    ap.add_argument("--serve", default="400:2,60:4",
+    ap.add_argument("--serve", default="400:2,60:10",
                     help="serving traces as rate_hz:seconds pairs ('' = skip serving)")
     ap.add_argument("--serve-capacity", type=int, default=1 << 28)
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)

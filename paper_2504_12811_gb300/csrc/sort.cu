@@ -130,10 +130,11 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __
     for (int j = 0; j < ITEMS; ++j) {
       const uint32_t d = (k[j] >> shift) & 0xffu;
       const unsigned peers = __match_any_sync(0xffffffffu, d);
-      const uint32_t before = s_warp[warp][d];
-      __syncwarp();
-      if ((peers & lt) == 0) s_warp[warp][d] = before + __popc(peers);
-      __syncwarp();
+      // the lowest lane of each digit group claims the group's ranks
+      const int leader = __ffs(peers) - 1;
+      uint32_t before = 0;
+      if (lane == leader) before = atomicAdd(&s_warp[warp][d], (uint32_t)__popc(peers));
+      before = __shfl_sync(0xffffffffu, before, leader);
       r[j] = before + __popc(peers & lt);
     }
     __syncthreads();
