@@ -28,7 +28,7 @@ constexpr unsigned long long kFlagAggregate = 1ull << 30;
 constexpr unsigned long long kFlagPrefix = 2ull << 30;
 constexpr unsigned long long kCountMask = (1ull << 30) - 1ull;
 constexpr long long kWaitCycles = 2000000000ll;   // ~1 s at 2 GHz
-constexpr int kLookWindow = 8;                    // look-back words loaded per round trip
+constexpr int kLookWindow = 4;                    // look-back words loaded per round trip
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -115,11 +115,12 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __
 
     // ---- load (warp-striped: coalesced) and rank within each warp
     uint32_t k[ITEMS], v[ITEMS], r[ITEMS];
-    const int64_t base = tile * kTileKeys + (int64_t)warp * (32 * ITEMS);
+    const uint32_t n32 = (uint32_t)n;
+    const uint32_t base = (uint32_t)tile * kTileKeys + (uint32_t)warp * (32 * ITEMS) + (uint32_t)lane;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-      const int64_t idx = base + j * 32 + lane;
-      const bool ok = idx < n;
+      const uint32_t idx = base + j * 32;
+      const bool ok = idx < n32;
       k[j] = ok ? keys_in[idx] : 0xffffffffu;
       v[j] = ok ? vals_in[idx] : 0u;
     }
@@ -210,16 +211,15 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __
       s_vals[pos] = v[j];
     }
     __syncthreads();
-    const int64_t valid = min((int64_t)kTileKeys, n - tile * kTileKeys);
-    for (int q = tid; q < kTileKeys; q += kSortThreads) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int q = tid + i * kSortThreads;
       const uint32_t key = s_keys[q];
       const uint32_t d = (key >> shift) & 0xffu;
-      const int64_t g = (int64_t)s_global[d] + (q - (int64_t)s_digit_start[d]);
-      if (q < valid || g < n) {
-        if (g < n) {
-          keys_out[g] = key;
-          vals_out[g] = s_vals[q];
-        }
+      const uint32_t g = s_global[d] + ((uint32_t)q - s_digit_start[d]);
+      if (g < n32) {
+        keys_out[g] = key;
+        vals_out[g] = s_vals[q];
       }
     }
     __syncthreads();
