@@ -222,13 +222,14 @@ __device__ __forceinline__ void release_rounds(SmemQueue<Q>& q, Blender& bl, Wan
 // Traverse one tile for one pixel.  Blender must provide:
 //   using Queue;                                     its queue store
 //   bool done;                                       pixel finished
-//   void blend(float alpha, Queue::Payload);         blend a queued contributor
 //   void blend_new(float alpha, const EvalState&);   blend the staged Gaussian k
 //   Queue::Payload payload(int k);                   what a queued entry of k carries
 //   void begin_batch(uint32_t b0, int cnt);          pairs b0 .. b0+cnt-1 are staged
+// and, without CONVERGENT (each lane releases in its own loop),
+//   void blend(float alpha, Queue::Payload);         blend a queued contributor
 // With CONVERGENT, every lane runs every iteration (no early exit from the
-// pair loop), every release is a warp-wide round, and the Blender also
-// provides
+// pair loop), every release is a warp-wide round, and the Blender provides
+// instead
 //   void release_round(bool w, float a, Queue::Payload);   warp-converged; lanes
 //                                                    with w blend the popped entry
 //   void end_item(int k);                            warp-converged, after item k
