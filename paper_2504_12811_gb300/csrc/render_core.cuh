@@ -2,9 +2,12 @@
 //
 // Both kernels walk a tile's sorted pairs with identical arithmetic (explicit
 // fmaf everywhere, so the two compile to the same rounding), the same
-// per-pixel re-sort queue and the same release rule; they differ only in what
-// happens when a contributor is blended, which is a functor.  The backward
-// pass therefore replays exactly the blend sequence of the forward pass.
+// per-pixel re-sort queue and the same release rule; they differ in what
+// happens when a contributor is blended, which is a functor, and in how the
+// releases of a warp's lanes are scheduled (per lane in the forward, in
+// warp-wide rounds in the backward), which leaves each pixel's sequence
+// unchanged.  The backward pass therefore replays exactly the blend sequence
+// of the forward pass.
 //
 // Plane form (paper Sec. 3.1, Eq. 4-5): with t_i the rows of T_view and tile
 // origin (x_t, y_t), U = fx t1 + (cx - x_t) t3 and W = fy t2 + (cy - y_t) t3.
