@@ -244,6 +244,28 @@ def run_train_step(args, dev, flush):
             "blended_last_view": st["blended"], "scene_generation_s": t_gen}
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest value of x over the ranks of the process group (x itself
+    without one): the job's time is that of its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = (torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl"
+           else torch.device("cpu"))
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed (each the same
+    count) per second of the slowest rank's time."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    return units_per_rank * world / (max_over_ranks(ms) / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -475,12 +497,8 @@ def run_ours(args):
         frame(args.warmup + k, evs[k])
     torch.cuda.synchronize()
     stage = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(4)] for k in range(args.steps)])
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    frames = args.steps * world
-    value = frames / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms)
+    value = job_rate(args.steps, total_ms)
 
     # ---- ablations (Sec. 5): the same frames with one switch each
     ablation = {}
@@ -545,7 +563,7 @@ def run_ours(args):
     st_b = aaag.stats(ws, check=False)
     fb_ms = np.array([[bev[k][0].elapsed_time(bev[k][1]), bev[k][1].elapsed_time(bev[k][2])]
                       for k in range(bwd_steps)])
-    fwd_bwd_fps = bwd_steps / (fb_ms.sum() / 1e3) * world
+    fwd_bwd_fps = job_rate(bwd_steps, float(fb_ms.sum()))
 
     # ---- roofline of the dominant kernel (render, FP32 ALU bound)
     ev_by_step = [per_pose[(args.warmup + k) % len(poses)]["evaluations"] for k in range(args.steps)]
@@ -619,7 +637,7 @@ def run_ours(args):
         read[k].record(down)
     e1.record(down)
     torch.cuda.synchronize()
-    e2e_value = e2e_steps / (e0.elapsed_time(e1) / 1e3) * world
+    e2e_value = job_rate(e2e_steps, e0.elapsed_time(e1))
 
     # set_frame + preprocess test + preprocess; cull: offsets + test + emit;
     # sort: histogram + radix passes + ranges; render
