@@ -310,6 +310,21 @@ aaag_status aaag_graph_launch(aaag_graph* g, const aaag_camera* camera,
 void aaag_graph_destroy(aaag_graph* g);
 
 /* --------------------------------------------------------------------------
+ * aaag_selftest_wait_timeout -- failure detection without a fault: runs one
+ * of the library's bounded device-side waits against a predecessor that
+ * never publishes (which = 0: the warp look-back of aaag_cull's scans;
+ * which = 1: the per-digit look-back of the radix sort), on the workspace's
+ * own look-back words (their first entries are cleared; later frames carry
+ * new epochs and ignore them).  The wait gives up after about one second,
+ * raises the workspace's timeout flag and returns, so the context stays
+ * usable: aaag_get_stats then reports TIMEOUT until the next
+ * aaag_preprocess resets the frame statistics.  Asynchronous on stream.
+ * Errors: INVALID_ARG (null ws, which not 0 or 1), CUDA.
+ * ------------------------------------------------------------------------ */
+aaag_status aaag_selftest_wait_timeout(aaag_workspace* ws, int32_t which,
+                                       cudaStream_t stream);
+
+/* --------------------------------------------------------------------------
  * aaag_radix_sort -- the stable LSD radix sort used by aaag_sort, on caller
  * arrays: sorts keys[0..n) (low `key_bits` bits significant, 1..32) and
  * carries vals along.  keys_alt / vals_alt are ping-pong buffers of n

@@ -94,6 +94,7 @@ SIGNATURES = [
                                     C.POINTER(C.c_void_p)]),
     ("aaag_graph_launch", C.c_int, [C.c_void_p, C.POINTER(aaag_camera), C.c_void_p]),
     ("aaag_graph_destroy", None, [C.c_void_p]),
+    ("aaag_selftest_wait_timeout", C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     ("aaag_radix_sort_scratch_bytes", C.c_size_t, [C.c_int64]),
     ("aaag_radix_sort", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                   C.c_void_p, C.c_size_t, C.POINTER(C.c_int32), C.c_void_p]),
@@ -204,6 +205,10 @@ def aaag_graph_launch(graph, camera, stream):
 
 def aaag_graph_destroy(graph):
     lib().aaag_graph_destroy(graph)
+
+
+def aaag_selftest_wait_timeout(ws, which, stream):
+    _check(lib().aaag_selftest_wait_timeout(ws, which, stream), "aaag_selftest_wait_timeout")
 
 
 def aaag_radix_sort_scratch_bytes(n):

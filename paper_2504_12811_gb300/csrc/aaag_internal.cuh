@@ -144,6 +144,8 @@ aaag_status check_launch(const char* what);
 aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st);
 void prepare_cull_kernels();
+aaag_status launch_cull_wait_selftest(aaag_workspace* ws, cudaStream_t st);
+aaag_status launch_sort_wait_selftest(aaag_workspace* ws, cudaStream_t st);
 int64_t cull_lookback_words(int64_t n, int64_t chunk_cap);
 aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st);

@@ -674,6 +674,16 @@ aaag_status aaag_graph_launch(aaag_graph* g, const aaag_camera* camera, cudaStre
   return AAAG_OK;
 }
 
+aaag_status aaag_selftest_wait_timeout(aaag_workspace* ws, int32_t which, cudaStream_t stream) {
+  if (!ws || which < 0 || which > 1) {
+    set_error("aaag_selftest_wait_timeout: invalid argument");
+    return AAAG_ERR_INVALID_ARG;
+  }
+  if (cudaMemsetAsync(ws->stats + kStatTimeout, 0, sizeof(unsigned long long), stream) != cudaSuccess)
+    return check_launch("aaag_selftest_wait_timeout memset");
+  return which == 0 ? launch_cull_wait_selftest(ws, stream) : launch_sort_wait_selftest(ws, stream);
+}
+
 void aaag_graph_destroy(aaag_graph* g) {
   if (!g) return;
   cudaGraphExecDestroy(g->exec);

@@ -83,6 +83,15 @@ __device__ __forceinline__ unsigned long long warp_lookback(const volatile unsig
   }
 }
 
+// Self-test of the bounded wait: tile 1 waits on tile 0, whose word carries a
+// tag no frame uses (cleared first), so the warp gives up after kWaitCycles and
+// raises the flag.
+__global__ void cull_wait_selftest_kernel(unsigned long long* lb, unsigned long long* timeout_flag) {
+  if (threadIdx.x == 0) lb[0] = 0ull;
+  __syncwarp();
+  warp_lookback(lb, 1, lb_tag(0xfffffeull), timeout_flag);
+}
+
 // exclusive scan of one value per thread over the block; returns the block
 // total in *total (all threads)
 __device__ __forceinline__ unsigned long long block_scan(unsigned long long v, unsigned long long* wsum,
@@ -362,6 +371,11 @@ void init_cull_occupancy() {
 }  // namespace
 
 void prepare_cull_kernels() { init_cull_occupancy(); }
+
+aaag_status launch_cull_wait_selftest(aaag_workspace* ws, cudaStream_t st) {
+  cull_wait_selftest_kernel<<<1, 32, 0, st>>>(ws->cull_lookback, ws->stats + kStatTimeout);
+  return check_launch("cull wait self-test");
+}
 
 int64_t cull_lookback_words(int64_t n, int64_t chunk_cap) {
   return (n + kOffTile - 1) / kOffTile + (chunk_cap + kChunkTile - 1) / kChunkTile + 2;

@@ -88,6 +88,49 @@ struct SortSmem {
   int tile;
 };
 
+// Decoupled look-back of one digit (thread tid = digit) for tile `tile` > 0:
+// kLookWindow predecessor words per round trip, loaded together and consumed
+// nearest first until an inclusive prefix, or a word not yet published (then
+// the window is reloaded from there).  Returns the exclusive prefix.  The
+// wait is bounded: after kWaitCycles without progress the timeout flag is
+// raised and the prefix found so far returned.
+__device__ __forceinline__ uint32_t digit_lookback(const volatile unsigned long long* lb, int64_t tile, int tid,
+                                                   unsigned long long tag, unsigned long long* timeout_flag) {
+  uint32_t prefix = 0;
+  int64_t t = tile - 1;   // nearest predecessor not yet consumed
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned long long w[kLookWindow];
+#pragma unroll
+    for (int j = 0; j < kLookWindow; ++j)
+      w[j] = t - j >= 0 ? lb[(t - j) * kRadix + tid] : (tag | kFlagPrefix);   // tile 0 ends it first
+    int used = 0;
+    bool stop = false, stall = false;
+#pragma unroll
+    for (int j = 0; j < kLookWindow; ++j) {
+      if (!stop && !stall) {
+        const unsigned long long x = w[j];
+        if ((x & 0xffffffff00000000ull) != tag || (x & (3ull << 30)) == 0) {
+          stall = true;
+        } else {
+          prefix += (uint32_t)(x & kCountMask);
+          ++used;
+          stop = (x & kFlagPrefix) != 0;
+        }
+      }
+    }
+    if (stop) return prefix;
+    t -= used;
+    if (used == 0) {
+      if (clock64() - t0 > kWaitCycles) {
+        atomicExch(timeout_flag, 1ull);
+        return prefix;
+      }
+      __nanosleep(20);
+    }
+  }
+}
+
 // Tiles of ITEMS keys per thread, taken in order from the pass counter.
 template <int ITEMS>
 __device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __restrict__ keys_in,
@@ -157,46 +200,9 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __
     const uint32_t local_start = block_exclusive_scan_256(count, s_tmp);
     s_digit_start[tid] = local_start;
 
-    // ---- decoupled look-back for digit tid, kLookWindow predecessors per
-    // round trip: the words of tiles t, t-1, ... are loaded together and
-    // consumed nearest first until an inclusive prefix, or a word not yet
-    // published (then the window is reloaded from there)
     uint32_t prefix = 0;
     if (tile > 0) {
-      int64_t t = tile - 1;   // nearest predecessor not yet consumed
-      const long long t0 = clock64();
-      bool timed_out = false;
-      for (;;) {
-        unsigned long long w[kLookWindow];
-#pragma unroll
-        for (int j = 0; j < kLookWindow; ++j)
-          w[j] = t - j >= 0 ? lb[(t - j) * kRadix + tid] : (tag | kFlagPrefix);   // tile 0 ends it first
-        int used = 0;
-        bool stop = false, stall = false;
-#pragma unroll
-        for (int j = 0; j < kLookWindow; ++j) {
-          if (!stop && !stall) {
-            const unsigned long long x = w[j];
-            if ((x & 0xffffffff00000000ull) != tag || (x & (3ull << 30)) == 0) {
-              stall = true;
-            } else {
-              prefix += (uint32_t)(x & kCountMask);
-              ++used;
-              stop = (x & kFlagPrefix) != 0;
-            }
-          }
-        }
-        if (stop) break;
-        t -= used;
-        if (used == 0) {
-          if (clock64() - t0 > kWaitCycles) {
-            timed_out = true;
-            break;
-          }
-          __nanosleep(20);
-        }
-      }
-      if (timed_out) atomicExch(timeout_flag, 1ull);
+      prefix = digit_lookback(lb, tile, tid, tag, timeout_flag);
       lb[tile * kRadix + tid] = tag | kFlagPrefix | (unsigned long long)(prefix + count);
     }
     s_global[tid] = gofs + prefix;
@@ -224,6 +230,16 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __
     }
     __syncthreads();
   }
+}
+
+// Self-test of the bounded wait: digit tid of tile 1 waits on tile 0, whose
+// words carry a tag no pass uses (lb[0 .. kRadix) cleared first), so every
+// thread gives up after kWaitCycles and raises the flag.
+__global__ void sort_wait_selftest_kernel(unsigned long long* lb, unsigned long long* timeout_flag) {
+  lb[threadIdx.x] = 0ull;
+  __syncthreads();
+  const unsigned long long tag = 0xfffffffeull << 32;
+  digit_lookback(lb, 1, (int)threadIdx.x, tag, timeout_flag);
 }
 
 // Keys per thread by problem size: small sorts use small tiles so that every
@@ -321,6 +337,11 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
     std::swap(vin, vout);
   }
   return AAAG_OK;
+}
+
+aaag_status launch_sort_wait_selftest(aaag_workspace* ws, cudaStream_t st) {
+  sort_wait_selftest_kernel<<<1, kRadix, 0, st>>>(ws->sort_lookback, ws->stats + kStatTimeout);
+  return check_launch("sort wait self-test");
 }
 
 aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st) {
