@@ -60,9 +60,14 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, int deg, flo
 // Screen interval of one axis from the view-space tangent planes (Sec. 3.3,
 // Eq. 14-17).  Ai: row i of A = Rv R S' (view axis i of the Gaussian frame),
 // A3: the z row; mi, mz: view-space mean.  Returns false when the interval is
-// empty (the Gaussian lies behind the camera on this axis).
+// empty (the Gaussian lies behind the camera on this axis).  When the whole
+// tau-ellipsoid lies in front of the camera plane (in_front), x/z is
+// continuous over it and both tangent angles lie in (-pi/2, pi/2) around the
+// mean's, so the rotation step of Eq. 16 only orders them: the bounds are the
+// two slopes tan(theta) themselves, without the angles (the clamp of Eq. 17
+// is left to the pixel ranges, which only widens the interval).
 __device__ __forceinline__ bool axis_bounds(float3 Ai, float3 A3, float mi, float mz, float tau,
-                                            float f, float c, float eps, float& p1, float& p2) {
+                                            float f, float c, float eps, bool in_front, float& p1, float& p2) {
   const float sii = tau * dot3(Ai, Ai) - mi * mi;
   const float si3 = tau * dot3(Ai, A3) - mi * mz;
   const float S33 = tau * dot3(A3, A3);
@@ -79,6 +84,14 @@ __device__ __forceinline__ bool axis_bounds(float3 Ai, float3 A3, float mi, floa
     // roots of s33 tan^2 - 2 s13 tan + s11 = 0, numerically stable form
     const float sq = sqrtf(D);
     const float q = si3 + copysignf(sq, si3);
+    if (q != 0.0f && in_front) {
+      const float ta = q / s33, tb = sii / q;
+      p1 = f * fminf(ta, tb) + c;
+      p2 = f * fmaxf(ta, tb) + c;
+      p1 -= 0.01f + 1e-5f * fabsf(p1);
+      p2 += 0.01f + 1e-5f * fabsf(p2);
+      return true;
+    }
     if (q != 0.0f) {
       const float ra = atanf(q / s33);
       const float rb = atanf(sii / q);
@@ -332,8 +345,9 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev& s, const FrameCon
     bool ok = !inside && z_hi >= fc.znear;
     if (ok) {
       float px1, px2, py1, py2;
-      ok = axis_bounds(A1, A3, vx, vz, tau_c, fc.fx, fc.cx, fc.eps, px1, px2) &&
-           axis_bounds(A2, A3, vy, vz, tau_c, fc.fy, fc.cy, fc.eps, py1, py2);
+      const bool in_front = z_lo > 0.0f;
+      ok = axis_bounds(A1, A3, vx, vz, tau_c, fc.fx, fc.cx, fc.eps, in_front, px1, px2) &&
+           axis_bounds(A2, A3, vy, vz, tau_c, fc.fy, fc.cy, fc.eps, in_front, py1, py2);
       if (ok && z_lo < fc.znear && !eval2d) {
         near_bounds(A1, A3, vx, vz, tau_c, z_lo, z_hi, fc.fx, fc.cx, fc.znear, px1, px2);
         near_bounds(A2, A3, vy, vz, tau_c, z_lo, z_hi, fc.fy, fc.cy, fc.znear, py1, py2);
