@@ -192,9 +192,13 @@ aaag_status aaag_workspace_get_view(const aaag_workspace* ws,
  *   (Eq. 13); s_hat_i = s_i^2 + k / v_hat'^2; amplitude factor of Eq. 12;
  *   o_hat = o * factor; tau_rho = 2 ln(255 o_hat) (alpha >= 1/255 inside);
  *   discard when o_hat <= 1/255 or the camera is inside the tau-ellipsoid;
- *   view-space angular bounds of Eq. 14-17 -> tile rectangle; cull against
+ *   view-space angular bounds of Eq. 14-17 (for a Gaussian reaching in
+ *   front of znear, intersected with the bounds of its part beyond znear)
+ *   -> tile rectangle; cull against
  *   the whole image frustum truncated at znear (Eq. 18 over the image);
- *   SH colour; depth key from the front of the tau-ellipsoid.
+ *   SH colour; depth key: a lower bound of the depth t* of the maximum on
+ *   every ray the Gaussian contributes to (never below the front of its
+ *   tau-ellipsoid), quantised and rounded down.
  * Reads scene arrays; writes the workspace records.  scene->n, width and
  * height may be anything up to the workspace's maxima.  The frame constants
  * (camera, tiling, key layout) go to device memory through one single-thread
@@ -210,10 +214,14 @@ aaag_status aaag_preprocess(const aaag_scene* scene /* host struct */,
  * aaag_cull -- 3D frustum tile culling (Sec. 3.4, Eq. 18, and the near-plane
  * tile rule of Sec. 3.3): for every tile of a visible Gaussian's rectangle,
  * keep the tile iff min over the tile's frustum (planes through the tile
- * borders, truncated at znear) of rho^2 is below tau_rho; emit one
- * (key, Gaussian index) pair per kept tile, key = tile id (high bits) and the
- * quantised front depth (low bits).  Pairs beyond the capacity are dropped
- * and flagged (aaag_get_stats -> capacity_overflow).
+ * borders) of rho^2 is below tau_rho; for a Gaussian whose tau-ellipsoid
+ * reaches in front of znear, iff some point of the tile has rho^2 <= tau_rho
+ * with the ray's maximum at t* >= znear (the per-pixel near-plane rule over
+ * the tile's area).  Emits one (key, Gaussian index) pair per kept tile,
+ * key = tile id (high bits) and the quantised depth bound (low bits; the
+ * layout is in aaag_workspace_view).  Pairs beyond the capacity are dropped
+ * and flagged (aaag_get_stats -> capacity_overflow); a look-back wait that
+ * gives up sets the timeout flag.
  * Errors: INVALID_ARG, CUDA.
  * ------------------------------------------------------------------------ */
 aaag_status aaag_cull(aaag_workspace* ws, cudaStream_t stream);
