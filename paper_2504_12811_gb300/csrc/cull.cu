@@ -208,6 +208,41 @@ __device__ __forceinline__ bool tile_needed(float4 t1, float4 t2, float4 t3, flo
   return ct.hit(xlo, ylo, xhi, yhi);
 }
 
+// Depth key of a (Gaussian, tile) pair: the ray maximum of a pixel lies at
+// t* = G.d / |d|^2 (render_core.cuh), with d affine in the pixel centre and
+// G the Gaussian's constant vector.  Over the tile's pixel centres
+// (tile-relative x, y in [0.5, 15.5]) G.d is affine, so its minimum is at a
+// corner, and |d|^2 is convex, so its maximum is at a corner: when the
+// smallest corner value of G.d is positive, min G.d / max |d|^2 bounds t* from
+// below on every ray of the tile.  Lowered by 1e-5 relative (float32 rounding
+// of the render's t*), quantised like the Gaussian's own key and rounded down;
+// 0 (the smallest key) when no bound results.  The pair key is the larger of
+// this and the Gaussian's key: both are lower bounds, and a tighter one lets
+// more contributors blend at once instead of waiting in the per-pixel queue.
+__device__ __forceinline__ uint32_t tile_depth_key(float4 t1, float4 t2, float4 t3, const FrameConst& fc,
+                                                   int tx, int ty) {
+  const float cxm = fc.cx - (float)(tx * kTile), cym = fc.cy - (float)(ty * kTile);
+  const float3 T3 = f3(t3.x, t3.y, t3.z), A1 = f3(t1.x, t1.y, t1.z), A2 = f3(t2.x, t2.y, t2.z);
+  const float3 Uv = fc.fx * A1 + cxm * T3;
+  const float3 Wv = fc.fy * A2 + cym * T3;
+  const float3 D0 = cross3(Uv, Wv), Dx = cross3(Wv, T3), Dy = cross3(T3, Uv);
+  const float3 G = (fc.fx * fc.fy) * (t1.w * cross3(A2, T3) + t2.w * cross3(T3, A1) + t3.w * cross3(A1, A2));
+  float nmin = 3.0e38f, qmax = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float x = (k & 1) ? 15.5f : 0.5f, y = (k & 2) ? 15.5f : 0.5f;
+    const float3 d = D0 + x * Dx + y * Dy;
+    nmin = fminf(nmin, dot3(G, d));
+    qmax = fmaxf(qmax, dot3(d, d));
+  }
+  if (!(nmin > 0.0f) || !(qmax > 0.0f)) return 0u;
+  float z = nmin / qmax;
+  z -= 1e-5f * z + 1e-6f;
+  if (!(z > fc.znear)) return 0u;
+  const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
+  return min((__float_as_uint(z) - fc.znear_bits) >> fc.depth_shift, dmax);
+}
+
 // One warp per chunk (grid-stride), one lane per tile: the warp ballot of the
 // chunk's needed tiles is stored.
 __global__ void __launch_bounds__(kThreads, 3)
@@ -253,7 +288,7 @@ cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
 // its global pair offset by look-back, then each warp writes the pairs of its
 // 32 chunks in chunk order (lane i first loads the geometry of chunk i).
 __global__ void __launch_bounds__(kThreads)
-cull_emit_kernel(const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
+cull_emit_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
                  const uint32_t* __restrict__ owner, const uint32_t* __restrict__ chunk_offsets,
                  const uint32_t* __restrict__ n_chunks_dev, int64_t chunk_cap, const uint32_t* __restrict__ masks,
                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity,
@@ -343,8 +378,14 @@ cull_emit_kernel(const uint4* __restrict__ aux, const FrameConst* __restrict__ f
         const int j = li * 32 + lane;
         const uint64_t at = wbase + before + (uint64_t)__popc(mi & lt);
         if (at < (uint64_t)capacity) {
-          const uint32_t t = (uint32_t)((ty0 + j / nx) * fc.tiles_x + tx0 + j % nx);
-          keys[at] = (t << fc.depth_bits) | aw;
+          const int txi = tx0 + j % nx, tyi = ty0 + j / nx;
+          const uint32_t t = (uint32_t)(tyi * fc.tiles_x + txi);
+          uint32_t dk = aw;
+          if (!(fc.flags & (AAAG_FLAG_NO_RESORT | AAAG_FLAG_EVAL_2D))) {
+            const float4* r = reinterpret_cast<const float4*>(rec + gi);
+            dk = max(dk, tile_depth_key(__ldg(r + 0), __ldg(r + 1), __ldg(r + 2), fc, txi, tyi));
+          }
+          keys[at] = (t << fc.depth_bits) | dk;
           vals[at] = gi;
         }
       }
@@ -403,7 +444,7 @@ aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st) {
   if (e != AAAG_OK) return e;
   const int64_t tiles_b = std::max<int64_t>((ws->chunk_capacity + kChunkTile - 1) / kChunkTile, 1);
   const unsigned grid_b = (unsigned)std::min<int64_t>(tiles_b, (int64_t)g_sms * g_blocks_b);
-  cull_emit_kernel<<<grid_b, kThreads, 0, st>>>(ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets, n_chunks,
+  cull_emit_kernel<<<grid_b, kThreads, 0, st>>>(ws->records, ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets, n_chunks,
                                                 ws->chunk_capacity, ws->chunk_mask, ws->keys[0], ws->vals[0],
                                                 ws->capacity, look_b, ws->stats, n_pairs);
   return check_launch("cull_emit");
