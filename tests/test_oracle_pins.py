@@ -465,6 +465,85 @@ def test_camera_inside_discards():
     np.testing.assert_allclose(rgb.numpy(), rgb1.numpy(), atol=1e-15)
 
 
+def test_near_plane_rule_closed_form():
+    # Sec. 3.3: a contribution whose ray maximum lies in front of the near
+    # plane is dropped.  For an isotropic Gaussian on the optical axis at depth
+    # z0 and the ray of direction (x', y', 1), the maximum is the foot of the
+    # perpendicular from the mean, t* = z0 / (1 + x'^2 + y'^2): the centre
+    # pixels see t* ~ z0 > z_near, the pixels far enough off axis t* < z_near,
+    # while alpha stays far above 1/255 on all of them.
+    f = 40.0
+    cam = scenes.Camera(np.eye(4, dtype=np.float32), f, f, 16.0, 16.0, 32, 32)
+    znear = float(np.float32(scenes.ZNEAR))
+    assert cam.znear == znear
+    z0 = float(np.float32(0.22))
+    sc = one_gaussian_scene([[0.0, 0.0, z0]], [[math.log(0.04)] * 3], logit=3.0)
+    p = O.prepare(sc, cam)
+    assert bool(p["alive"][0])
+    px, py = np.arange(16, 32), np.full(16, 16)
+    rho2, ts = O.ray_maximum(p, px, py)
+    alpha, contrib, raw = O.pixel_alphas(p, rho2, ts)
+    xp, yp = (px + 0.5 - 16.0) / f, (py + 0.5 - 16.0) / f
+    t_closed = z0 / (1.0 + xp * xp + yp * yp)
+    np.testing.assert_allclose(ts[:, 0].numpy(), t_closed, rtol=1e-12)
+    bright = raw[:, 0].numpy() >= 10 * O.ALPHA_MIN
+    assert bright.all()
+    behind = t_closed < znear
+    assert 0 < behind.sum() < behind.size          # both sides of the plane occur
+    np.testing.assert_array_equal(contrib[:, 0].numpy(), ~behind)
+    # straddling z_near by 1e-9 relative: the rule is t* >= z_near
+    k = int(np.nonzero(~behind)[0][-1])
+    t_k = float(ts[k, 0])
+    for zn, expect in ((t_k * (1 + 1e-9), False), (t_k * (1 - 1e-9), True), (t_k, True)):
+        p["view"].znear = zn
+        _, c, _ = O.pixel_alphas(p, rho2[k:k + 1], ts[k:k + 1])
+        assert bool(c[0, 0]) == expect, (zn, t_k)
+    # and the image: the pixels behind the plane show the background only
+    p["view"].znear = znear
+    rgb, a = O.render_pixels(sc, cam, px, py, prep=p)
+    assert np.all(a.numpy()[behind] == 0.0) and np.all(a.numpy()[~behind] > 0.01)
+
+
+def test_cutoff_level_and_camera_inside_flip():
+    # tau_rho is the rho^2 at which o_hat exp(-rho^2/2) reaches 1/255
+    rng = np.random.default_rng(21)
+    oh = rng.uniform(O.ALPHA_MIN * (1 + 1e-6), 0.99, 1000)
+    tau = O.cutoff(torch.from_numpy(oh)).numpy()
+    np.testing.assert_allclose(oh * np.exp(-tau / 2), O.ALPHA_MIN, rtol=1e-12)
+    assert np.all(np.diff(tau[np.argsort(oh)]) > 0)
+    # An isotropic Gaussian of scale s on the optical axis at depth D, no
+    # training clamp: s_hat = s^2 + k D^2 / f^2 (Eq. 6, 13), o_hat =
+    # o s^2 / s_hat (Eq. 12, isotropic), tau = 2 ln(255 o_hat) and
+    # |u_cam|^2 = D^2 / s_hat.  The camera-inside discard (Sec. 3.3) must flip
+    # where |u_cam|^2 crosses tau, found here by bisection on these closed forms.
+    f, k = 50.0, O.K_FILTER
+    ls = np.float32(-2.0)
+    logit = np.float32(1.0)
+    s2 = math.exp(2.0 * float(ls))
+    o = 1.0 / (1.0 + math.exp(-float(logit)))
+
+    def closed(D):
+        sh = s2 + k * D * D / (f * f)
+        t = 2.0 * math.log(255.0 * o * s2 / sh)
+        return D * D / sh - t, t
+
+    lo, hi = 0.21, 5.0
+    assert closed(lo)[0] < 0 < closed(hi)[0]
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if closed(mid)[0] < 0 else (lo, mid)
+    cam = scenes.Camera(np.eye(4, dtype=np.float32), f, f, 8.0, 8.0, 16, 16)
+    for rel, inside in ((-1e-6, True), (1e-6, False)):
+        D = float(np.float32(lo * (1 + rel)))
+        g, t = closed(D)
+        assert (g < 0) == inside
+        sc = one_gaussian_scene([[0.0, 0.0, D]], [[ls] * 3], logit=logit)
+        p = O.prepare(sc, cam)
+        assert p["tau"][0].item() == pytest.approx(t, rel=1e-12)
+        assert bool(p["inside"][0]) == inside
+        assert bool(p["alive"][0]) == (not inside)
+
+
 def test_transmittance_monotone_and_alpha_range(small_workload):
     sc, cams = small_workload
     p = O.prepare(sc, cams[0])
