@@ -38,11 +38,10 @@ WORKLOAD = "scene1m: 1,000,000 Gaussians (64 clusters + 10% shell, SH 3), 1920x1
 # compares (~3), t* (~4) and the blend (~8): about 40.
 OPS_PER_EVAL = 40
 # Mean DRAM bytes (read + write) of one render launch over the 16 poses of the
-# workload, from an ncu capture of this kernel version (dram__bytes_read.sum +
-# dram__bytes_write.sum, cold cache).
-RENDER_DRAM_BYTES = 16.33e6
+# workload, from an ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum, cold cache); None until one is taken.
+RENDER_DRAM_BYTES = None
 FP32_LANES_PER_SM = 128
-SMS = 152
 
 
 def parse():
@@ -60,7 +59,53 @@ def parse():
                     help="serving traces as rate_hz:seconds pairs ('' = skip serving)")
     ap.add_argument("--serve-capacity", type=int, default=1 << 28)
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
+    ap.add_argument("--sort-keys", type=int, default=0,
+                    help="only time aaag_radix_sort on this many random keys with values and exit")
+    ap.add_argument("--sort-bits", type=int, default=32)
+    ap.add_argument("--sort-reps", type=int, default=5)
     return ap.parse_args()
+
+
+def run_sort_only(args):
+    """Time the radix sort entry point (aaag_radix_sort) alone: N uniform
+    random keys (low B bits) with their indices as values, R timed calls
+    after one warm-up; prints ms per sort and bytes moved per second (each
+    pass reads and writes key and value, plus one histogram read)."""
+    import torch
+    from paper_2504_12811_gb300 import aaag, build as B
+    B.build()
+    dev = torch.device("cuda", 0)
+    n, bits = args.sort_keys, args.sort_bits
+    g = torch.Generator(device=dev)
+    g.manual_seed(1)
+    k0 = torch.randint(0, 1 << min(bits, 31), (n,), device=dev, dtype=torch.int64, generator=g).to(torch.int32)
+    v0 = torch.arange(n, device=dev, dtype=torch.int32)
+    keys, vals = k0.clone(), v0.clone()
+    ka, va = torch.empty_like(keys), torch.empty_like(vals)
+    sb = aaag.aaag_radix_sort_scratch_bytes(n)
+    scratch = torch.zeros(sb, dtype=torch.uint8, device=dev)
+    st = aaag.current_stream()
+    ms = []
+    alt = 0
+    for rep in range(args.sort_reps + 1):
+        keys.copy_(k0)
+        vals.copy_(v0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        alt = aaag.aaag_radix_sort(keys.data_ptr(), vals.data_ptr(), ka.data_ptr(), va.data_ptr(), n, bits,
+                                   scratch.data_ptr(), sb, st)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep:
+            ms.append(e0.elapsed_time(e1))
+    out = ka if alt else keys
+    ok = bool((out[1:].to(torch.int64) >= out[:-1].to(torch.int64)).all())
+    passes = (bits + 7) // 8
+    t = sum(ms) / len(ms)
+    print(json.dumps({"keys": n, "key_bits": bits, "ms": t, "gbs": n * (16 * passes + 4) / (t / 1e3) / 1e9,
+                      "sorted": ok}))
+    if not ok:
+        raise SystemExit("not sorted")
 
 
 def run_serving(args, dev):
@@ -198,8 +243,9 @@ def run_hbm_large(dev, flush, hbm_peak, n=16_000_000, n_keys=64 << 20):
 def run_train_step(args, dev, flush):
     """Forward + backward of each of the 4 views of the 500k-Gaussian
     training workload (1280x832, SH 3): the rendering work of one training
-    step over those views.  This scene is dense enough that the per-pixel
-    buffer overflows: the order is approximate there."""
+    step over those views.  This scene is dense enough that most pixels hold
+    more waiting contributors than the per-pixel buffer: they take further
+    depth-peeling passes (exact order)."""
     import numpy as np
     import torch
     from paper_2504_12811_gb300 import aaag, scenes
@@ -241,6 +287,7 @@ def run_train_step(args, dev, flush):
     return {"workload": "train500k: 500,000 Gaussians (uniform cube, SH 3), 4 views of 1280x832",
             "ms_per_step": ms, "views_per_s": 4e3 / ms, "status": st["status"],
             "pairs_last_view": st["n_pairs"], "misorders_last_view": st["misorders"],
+            "extra_passes_last_view": st["extra_passes"],
             "blended_last_view": st["blended"], "scene_generation_s": t_gen}
 
 
@@ -330,12 +377,58 @@ def load_workload():
     return scene, poses, time.time() - t
 
 
+def cpu_model() -> str:
+    """CPU model name of this host (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_frame_seconds(scene, cam, fraction=1.0, seed=0):
+    """Seconds of the oracle (as it stands) for one frame of `cam`: its
+    preparation of every Gaussian plus every pixel, or a seeded random
+    `fraction` of the pixels with the pixel time scaled to the full frame."""
+    import numpy as np
+    import oracle as O
+    t0 = time.time()
+    prep = O.prepare(scene, cam)
+    t_prep = time.time() - t0
+    py, px = np.mgrid[0:cam.height, 0:cam.width]
+    px, py = px.ravel(), py.ravel()
+    if fraction < 1.0:
+        sel = np.random.default_rng(seed).choice(px.size, max(1, int(px.size * fraction)), replace=False)
+        px, py = px[sel], py[sel]
+    t1 = time.time()
+    O.render_pixels(scene, cam, px, py, prep=prep)
+    return t_prep + (time.time() - t1) * (cam.width * cam.height) / px.size
+
+
 def cpu_baseline(scene, poses, seconds, unit_pixels):
-    """Time the oracle as it stands on a bounded pixel sample of pose 0.
-    Returns (frames/s equivalent, sample description, threads)."""
+    """Time the oracle as it stands on the host cores.
+
+    Headline unit (1M Gaussians, 1920x1080): preparation of pose 0 plus a
+    bounded random pixel sample, extrapolated to the frame.  Beside it, full
+    frames of the oracle-sized workloads (4,096 Gaussians: 128x128 at
+    distance 3; 480x270 zoom-out; 128x128 near-camera; the 2048x2048
+    120-degree view on a 1/64 pixel sample), on all cores and on one core
+    (the one-core zoom-out on a 1/8 sample).  Returns (frames/s, sample
+    description, threads, frame seconds, per-workload figures)."""
     import numpy as np
     import torch
     import oracle as O
+    from paper_2504_12811_gb300 import scenes
     cam = poses[0]
     t0 = time.time()
     prep = O.prepare(scene, cam)
@@ -352,10 +445,26 @@ def cpu_baseline(scene, poses, seconds, unit_pixels):
         done += batch
     per_pixel = t_pix / done
     frame_s = t_prep + per_pixel * unit_pixels
-    desc = (f"pose 0: oracle preparation of all {scene.n} Gaussians ({t_prep:.2f} s) + "
-            f"{done} random pixels ({t_pix:.2f} s); frame time extrapolated to "
-            f"{unit_pixels} pixels")
-    return 1.0 / frame_s, desc, torch.get_num_threads(), frame_s
+    desc = (f"scene1m pose 0, extrapolated: oracle preparation of all {scene.n} Gaussians ({t_prep:.2f} s) + "
+            f"{done} random pixels ({t_pix:.2f} s) scaled to {unit_pixels} pixels")
+    threads = torch.get_num_threads()
+    small = {}
+    plan = (("small", 1.0, 1.0), ("near", 1.0, 1.0), ("zoomout", 1.0, 0.125), ("widefov", 1.0 / 64, None))
+    for wl, frac_all, frac_one in plan:
+        sc, cams = scenes.workload(wl)
+        c = cams[0]
+        entry = {"gaussians": sc.n, "size": f"{c.width}x{c.height}"}
+        s_all = oracle_frame_seconds(sc, c, frac_all)
+        entry["all_cores"] = {"frames_per_s": 1.0 / s_all, "threads": threads, "pixel_fraction": frac_all}
+        if frac_one is not None:
+            torch.set_num_threads(1)
+            try:
+                s_one = oracle_frame_seconds(sc, c, frac_one)
+            finally:
+                torch.set_num_threads(threads)
+            entry["one_core"] = {"frames_per_s": 1.0 / s_one, "threads": 1, "pixel_fraction": frac_one}
+        small[wl] = entry
+    return 1.0 / frame_s, desc, threads, frame_s, small
 
 
 def run_reference(args):
@@ -570,7 +679,8 @@ def run_ours(args):
     render_ms = stage[:, 3]
     achieved_tflops = float(np.sum(np.array(ev_by_step) * OPS_PER_EVAL) / (render_ms.sum() / 1e3) / 1e12)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     # preprocess + cull + sort: algorithmic bytes vs measured HBM peak
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -665,7 +775,8 @@ def run_ours(args):
                     "replay_mismatch": int(st_b["replay_mismatch"])},
         "roofline": {"kernel": "render", "bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved_tflops / peak_tflops, "traffic": RENDER_DRAM_BYTES,
-                     "peak_source": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                     "peak_source": f"{sms} SMs (device query) x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                    f"{sm_max:.0f} MHz (max SM clock, nvidia-smi)",
                      "ops_per_evaluation": OPS_PER_EVAL},
         "hbm": {"preprocess_gbs": pre_gbs, "sort_gbs": sort_gbs, "peak_gbs": hbm_peak,
                 "peak_source": hbm_src, "preprocess_frac": pre_gbs / hbm_peak,
@@ -687,9 +798,12 @@ def run_ours(args):
     if args.serve:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, cores, frame_s = cpu_baseline(scene, poses, args.cpu_seconds, W * H)
+        v, desc, cores, frame_s, small = cpu_baseline(scene, poses, args.cpu_seconds, W * H)
         line["cpu_baseline"] = {"value": v, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                                "sample": desc}
+                                "sample": desc, "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+                                "oracle_sized_frames": small,
+                                "note": "frames/s of the FP64 oracle; a pixel_fraction below 1 times that "
+                                        "share of the pixels and scales the pixel time to the frame"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -698,7 +812,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.sort_keys:
+        run_sort_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

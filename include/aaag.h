@@ -87,10 +87,13 @@ typedef struct {
  * per-pixel re-sort */
 #define AAAG_FLAG_NO_RESORT 4u
 /* bounded-buffer approximate re-sort (the per-ray sorting the paper retains
- * from hierarchical rasterisation): contributors wait in the 16-entry
- * per-pixel buffer, which releases its nearest entry only when full and the
- * rest at the end; no release by key, so the order is exact only while the
- * buffer never fills */
+ * from hierarchical rasterisation): pairs are keyed by the view depth of the
+ * mean (clamped to z_near), so contributors arrive in that order (ties by
+ * Gaussian index); they wait in the 16-entry per-pixel buffer, ordered by
+ * (t*, arrival); an arrival that finds it full blends the nearest of the
+ * buffer and itself (the older on a tie), and the rest is blended nearest
+ * first at the end; no release by key and no further pass, so the order is
+ * exact only while the buffer never fills */
 #define AAAG_FLAG_KBUFFER   8u
 /* ablation without 3D evaluation (Sec. 5, 'w/o 3D'): each Gaussian is
  * splatted in 2D, its filtered covariance projected with the Jacobian of the
@@ -118,7 +121,13 @@ typedef struct {
   uint64_t tiles_tested;   /* tiles inside the bounds that were culled/kept */
   uint64_t evaluations;    /* pixel x Gaussian evaluations in aaag_render   */
   uint64_t blended;        /* contributors blended                          */
-  uint64_t misorders;      /* forced emissions of the per-pixel buffer      */
+  uint64_t misorders;      /* early releases of the per-pixel buffer in the
+                              bounded-buffer ablation (AAAG_FLAG_KBUFFER);
+                              0 otherwise: the default order is exact       */
+  uint64_t extra_passes;   /* depth-peeling passes beyond the first, summed
+                              over pixels (a pixel whose buffer filled
+                              defers its farthest contributors to another
+                              pass over its tile)                           */
   uint64_t replay_mismatch;/* pixels whose backward replay blended a count
                               different from the forward pass (expected 0)  */
   uint32_t capacity_overflow;  /* 1 when n_pairs > pair_capacity            */
@@ -244,10 +253,12 @@ aaag_status aaag_sort(aaag_workspace* ws, cudaStream_t stream);
  * along the pixel ray rho^2 = |h1 n2 - h2 n1|^2 / |n1 x n2|^2 from the planes
  * pi' = T'^T pi_x, T'^T pi_y (Eq. 4-5) and the depth t* of that maximum;
  * alpha = min(0.99, o_hat exp(-rho^2/2)); contributors with alpha >= 1/255
- * and t* >= znear are re-sorted per pixel by t* in a register buffer that
+ * and t* >= znear are re-sorted per pixel by t* in a 16-entry buffer that
  * releases an entry once every later pair of the tile is known to lie behind
- * it (per-ray sorting, Sec. 4 'Implementation Details'); front-to-back
- * blending stops before transmittance would fall below 1e-4.
+ * it (per-ray sorting, Sec. 4 'Implementation Details'); when the buffer is
+ * full the farthest contributors are deferred to another pass over the tile
+ * (depth peeling), so every pixel blends in exact (t*, pair order) order;
+ * front-to-back blending stops before transmittance would fall below 1e-4.
  * Writes rgb[3][H][W] = C + T * bg and alpha[H][W] = 1 - T (device,
  * caller-owned), plus final T and blended counts in the workspace.
  * Errors: INVALID_ARG (null outputs), CUDA.
@@ -326,8 +337,11 @@ void aaag_graph_destroy(aaag_graph* g);
  * new epochs and ignore them).  The wait gives up after about one second,
  * raises the workspace's timeout flag and returns, so the context stays
  * usable: aaag_get_stats then reports TIMEOUT until the next
- * aaag_preprocess resets the frame statistics.  Asynchronous on stream.
- * Errors: INVALID_ARG (null ws, which not 0 or 1), CUDA.
+ * aaag_preprocess resets the frame statistics.  which = 2 runs the sort's
+ * wait on the fixed array of aaag_radix_sort_static instead (ws may be
+ * NULL); aaag_radix_sort_static_status then reports TIMEOUT until the next
+ * aaag_radix_sort_static.  Asynchronous on stream.
+ * Errors: INVALID_ARG (null ws for which 0 or 1, which not 0, 1 or 2), CUDA.
  * ------------------------------------------------------------------------ */
 aaag_status aaag_selftest_wait_timeout(aaag_workspace* ws, int32_t which,
                                        cudaStream_t stream);
@@ -336,7 +350,9 @@ aaag_status aaag_selftest_wait_timeout(aaag_workspace* ws, int32_t which,
  * aaag_radix_sort -- the stable LSD radix sort used by aaag_sort, on caller
  * arrays: sorts keys[0..n) (low `key_bits` bits significant, 1..32) and
  * carries vals along.  keys_alt / vals_alt are ping-pong buffers of n
- * elements; scratch is aaag_radix_sort_scratch_bytes(n) bytes.  The result
+ * elements; scratch is aaag_radix_sort_scratch_bytes(n) bytes (16-byte
+ * aligned), zeroed by the caller before its first use and then kept as the
+ * calls leave it (it holds the look-back words and their epoch).  The result
  * ends in (keys, vals) when the number of 8-bit passes is even, else in
  * (keys_alt, vals_alt); *result_in_alt (host) says which.  n is a host
  * value here.  Errors: INVALID_ARG, CAPACITY (scratch too small), CUDA.
@@ -364,13 +380,21 @@ aaag_status aaag_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
  * capture.  All calls share the array: two calls that overlap on the GPU
  * (different streams, or different threads without ordering) race and give
  * wrong results; order them on one stream.  A look-back wait that gives up
- * leaves the output unspecified (no trap, no hang).
+ * leaves the output unspecified (no trap, no hang) and raises a flag in the
+ * array that aaag_radix_sort_static_status reports.
  * Errors: INVALID_ARG (n < 0, key_bits out of range, null arrays),
  * CAPACITY (n > capacity), CUDA.
  * ------------------------------------------------------------------------ */
 int64_t aaag_radix_sort_static_capacity(void);
 aaag_status aaag_radix_sort_static(uint32_t* keys, uint32_t* vals, int64_t n,
                                    int32_t key_bits, cudaStream_t stream);
+/* Outcome of the last aaag_radix_sort_static on the current device: reads the
+ * timeout flag of its bounded look-back waits from the fixed array (a
+ * synchronous device-to-host copy of 8 bytes; nothing is allocated).  Call it
+ * after synchronising the stream of that sort.  Returns OK, TIMEOUT (a wait
+ * gave up and that call's output is unspecified) or CUDA.  Each
+ * aaag_radix_sort_static clears the flag when it starts. */
+aaag_status aaag_radix_sort_static_status(void);
 
 /* --------------------------------------------------------------------------
  * aaag_vhat_train -- the training sampling frequency of every Gaussian (Sec.

@@ -22,7 +22,7 @@ __all__ = [
     "ray_maximum", "pixel_alphas", "composite", "render_pixels", "render",
     "view_space_bounds", "frustum_constraints", "frustum_min_rho2",
     "tile_min_rho2", "ambiguous_pixels", "scene_tensors", "training_sampling_frequency",
-    "ewa_splats", "splat_maximum",
+    "ewa_splats", "splat_maximum", "composite_kbuffer", "KBUFFER_SIZE",
 ]
 
 F64 = torch.float64
@@ -32,6 +32,7 @@ ALPHA_MAX = 0.99          # alpha clamp (3DGS convention)
 T_STOP = 1e-4             # early termination threshold on transmittance
 K_FILTER = 0.3            # filter size k (Sec. 4, implementation details)
 EPS_ANGLE = 1e-3          # epsilon of the angle clamp (Sec. 3.3, Eq. 17)
+KBUFFER_SIZE = 16         # entries of the bounded per-pixel buffer (ablation)
 
 
 def t64(a) -> torch.Tensor:
@@ -369,6 +370,84 @@ def composite(alpha, tstar, contrib, rgb, bg):
     return out, T, blended.sum(1)
 
 
+def composite_kbuffer(alpha, tstar, arrival, contrib, rgb, bg, size=KBUFFER_SIZE, sequences=False):
+    """Front-to-back compositing through a bounded per-pixel buffer, the
+    approximate per-ray re-sort that hierarchical rasterisation keeps
+    (Sec. 3.1 'Blending Sort Order'; the sort ablations of Sec. 5).
+
+    The contributors of a pixel arrive in the order of `arrival` (one key per
+    Gaussian, ties by Gaussian index).  The buffer holds up to `size` of them
+    ordered by (t*, arrival).  An arrival that finds the buffer full blends the
+    nearest of the buffer's entries and itself (the older one on a tie) and
+    keeps the others; when every contributor has arrived the buffer is blended
+    nearest first.  Blending stops before the contributor that would take T
+    below 1e-4.  The order is exact while no pixel holds more than `size`
+    contributors at once.  size = 0 blends in arrival order.  Plain float64
+    loops over pixels (no autograd).  Returns (RGB + T bg [P,3], final T [P],
+    blended count [P]), and with `sequences` also the blended Gaussians of
+    every pixel in blend order (a list of index arrays)."""
+    a_np = alpha.detach().numpy()
+    t_np = tstar.detach().numpy()
+    c_np = contrib.detach().numpy()
+    col = rgb.detach().numpy()
+    bgv = bg.detach().numpy()
+    arr = np.asarray(arrival, dtype=np.float64)
+    P = a_np.shape[0]
+    out = np.zeros((P, 3))
+    Tout = np.ones(P)
+    nb = np.zeros(P, dtype=np.int64)
+    seqs = []
+    for p in range(P):
+        gs = np.nonzero(c_np[p])[0]
+        gs = gs[np.lexsort((gs, arr[gs]))]                # arrival order
+        T, C, n = 1.0, np.zeros(3), 0
+        done = False
+        seq = []
+
+        def blend(g):
+            nonlocal T, C, n, done
+            Tn = T * (1.0 - a_np[p, g])
+            if Tn < T_STOP:
+                done = True
+                return
+            C = C + col[g] * (a_np[p, g] * T)
+            T = Tn
+            n += 1
+            seq.append(g)
+
+        buf = []                                           # sorted (t*, arrival rank, g)
+        for rank, g in enumerate(gs):
+            if done:
+                break
+            e = (t_np[p, g], rank, g)
+            if size == 0:
+                blend(g)
+                continue
+            if len(buf) == size:
+                if e < buf[0]:
+                    blend(g)
+                    continue
+                blend(buf.pop(0)[2])
+                if done:
+                    break
+            lo_, hi_ = 0, len(buf)
+            while lo_ < hi_:                               # insert after smaller keys
+                mid = (lo_ + hi_) // 2
+                if buf[mid] < e:
+                    lo_ = mid + 1
+                else:
+                    hi_ = mid
+            buf.insert(lo_, e)
+        while buf and not done:
+            blend(buf.pop(0)[2])
+        out[p] = C + T * bgv
+        Tout[p] = T
+        nb[p] = n
+        seqs.append(np.asarray(seq, dtype=np.int64))
+    res = (torch.from_numpy(out), torch.from_numpy(Tout), torch.from_numpy(nb))
+    return res + (seqs,) if sequences else res
+
+
 def ewa_splats(prep):
     """Ablation without 3D evaluation (Sec. 5, 'w/o 3D'): every Gaussian as a
     2D splat.  The filtered world covariance R diag(s_hat) R^T is taken to
@@ -405,13 +484,15 @@ def splat_maximum(prep, px, py, splats=None):
 
 
 def render_pixels(scene, cam, px, py, k: float = K_FILTER, chunk: int = 512,
-                  prep=None, order: str = "tstar", eval2d: bool = False):
+                  prep=None, order: str = "tstar", eval2d: bool = False, kbuffer: int = KBUFFER_SIZE):
     """RGB [P,3] and alpha [P] of the given pixels (plain definition: every
     Gaussian tested against every pixel).  order="tstar" blends in exact
     per-pixel order of the maxima; order="mean" is the sort ablation of
     Sec. 5 (no per-ray sorting): contributors blended in the order of the view
     depth of their means, clamped to z_near (reading: the same clamp as the
-    depth keys), ties by Gaussian index.  eval2d=True is the ablation without
+    depth keys), ties by Gaussian index; order="kbuffer" is the bounded-buffer
+    re-sort (`composite_kbuffer`, `kbuffer` entries) with contributors arriving
+    in that mean-depth order.  eval2d=True is the ablation without
     3D evaluation: alpha from the EWA splats (`ewa_splats`), depth the mean's,
     and (reading) no camera-inside rule: a Gaussian is alive when o_hat >
     1/255 and its mean lies beyond the near plane."""
@@ -433,6 +514,12 @@ def render_pixels(scene, cam, px, py, k: float = K_FILTER, chunk: int = 512,
         else:
             rho2, tstar = ray_maximum(prep, px[i:i + step], py[i:i + step])
             alpha, contrib, _ = pixel_alphas(prep, rho2, tstar)
+        if order == "kbuffer":
+            arrival = torch.clamp(prep["mu_view"][:, 2].detach(), min=prep["view"].znear).numpy()
+            out, T, _ = composite_kbuffer(alpha, tstar, arrival, contrib, prep["rgb"], prep["view"].bg, kbuffer)
+            outs.append(out)
+            Ts.append(T)
+            continue
         if order == "mean":
             key = torch.clamp(prep["mu_view"][:, 2].detach(), min=prep["view"].znear).expand_as(tstar)
         elif order == "tstar":
@@ -447,11 +534,13 @@ def render_pixels(scene, cam, px, py, k: float = K_FILTER, chunk: int = 512,
     return out, 1.0 - T
 
 
-def render(scene, cam, k: float = K_FILTER, prep=None, order: str = "tstar", eval2d: bool = False):
+def render(scene, cam, k: float = K_FILTER, prep=None, order: str = "tstar", eval2d: bool = False,
+           kbuffer: int = KBUFFER_SIZE):
     """Full image: RGB [3,H,W] and alpha [H,W] (float64)."""
     W, H = int(cam.width), int(cam.height)
     py, px = np.mgrid[0:H, 0:W]
-    out, alpha = render_pixels(scene, cam, px.ravel(), py.ravel(), k, prep=prep, order=order, eval2d=eval2d)
+    out, alpha = render_pixels(scene, cam, px.ravel(), py.ravel(), k, prep=prep, order=order, eval2d=eval2d,
+                               kbuffer=kbuffer)
     return out.T.reshape(3, H, W), alpha.reshape(H, W)
 
 
@@ -611,17 +700,26 @@ def tile_min_rho2(prep, gauss_idx, tile_x, tile_y, near: bool = True):
 # pixels where float32 rounding can legitimately flip a discrete decision
 # ---------------------------------------------------------------------------
 
-def ambiguous_pixels(prep, px, py, rel_alpha=2e-5, rel_t=2e-6, rel_tau=1e-4, swap=2e-4, eval2d=False):
-    """Pixels whose result depends on a decision that float32 evaluation may
-    take differently from float64 (test tolerance logic, not part of the
-    method):
-      * an alpha within rel_alpha (relative) of 1/255;
-      * a depth t* within rel_t (relative) of z_near for a contributor;
-      * a Gaussian whose camera-inside test or o_hat > 1/255 test is within
-        rel_tau of its threshold, touching the pixel;
-      * two depth-adjacent contributors whose t* differ by less than rel_t
-        (relative) and whose swap would change the pixel by more than `swap`
-        (swapping a before b changes C by T_a alpha_a alpha_b (c_a - c_b)).
+def ambiguous_pixels(prep, px, py, rel_alpha=2e-5, rel_t=2e-6, rel_tau=1e-4, budget=1e-3, eval2d=False):
+    """Pixels whose result may depend on a decision that float32 evaluation
+    can take differently from float64 (test tolerance logic, not part of the
+    method).  Candidate flips at a pixel:
+      * a Gaussian whose alpha lies within rel_alpha (relative) of 1/255;
+      * a contributor whose depth t* lies within rel_t (relative) of z_near;
+      * a Gaussian touching the pixel whose camera-inside test or o_hat > 1/255
+        test lies within rel_tau of its threshold;
+      * two depth-adjacent contributors whose t* differ by at most rel_t
+        (relative), which float32 may blend in either order.
+    Front-to-back compositing bounds what each flip can do: a layer of opacity
+    a entering or leaving at transmittance T (the product of 1 - alpha of the
+    contributors in front of it) moves every output channel by at most
+    a T cmax (cmax: the largest colour at the pixel, the background and 1 for
+    alpha), and swapping adjacent layers a, b by T_a a_a a_b |c_a - c_b|; a
+    flip next to early termination can also move the stopping point, by at
+    most T_STOP cmax.  A pixel is flagged when the bounds of its candidate
+    flips add up to more than `budget` (half the max-abs tolerance of the
+    parity tests), so that in dense content the hundreds of layers hidden
+    behind the opaque front do not flag pixels they cannot change.
     eval2d: the same for the 2D-splat ablation (no camera-inside test)."""
     view = prep["view"]
     if eval2d:
@@ -630,32 +728,45 @@ def ambiguous_pixels(prep, px, py, rel_alpha=2e-5, rel_t=2e-6, rel_tau=1e-4, swa
     else:
         rho2, tstar = ray_maximum(prep, px, py)
         live = prep["alive"].unsqueeze(0)
-    raw = prep["o_hat"].unsqueeze(0) * torch.exp(-0.5 * rho2)
-    near_alpha = (raw - ALPHA_MIN).abs() < rel_alpha * ALPHA_MIN
-    contrib = live & (raw >= ALPHA_MIN) & (tstar >= view.znear)
-    near_z = ((tstar - view.znear).abs() < rel_t * view.znear) & (raw >= ALPHA_MIN * (1 - rel_alpha))
-    uu = (prep["u_cam"] ** 2).sum(-1)
-    edge_g = (prep["o_hat"] - ALPHA_MIN).abs() < rel_tau * ALPHA_MIN
-    if not eval2d:
-        edge_g = edge_g | ((uu - prep["tau"]).abs() < rel_tau * prep["tau"].abs())
-    touched = raw >= ALPHA_MIN * (1 - rel_alpha)
-    flag = ((near_alpha | near_z) & (live | edge_g.unsqueeze(0))).any(1)
-    flag |= (touched & edge_g.unsqueeze(0)).any(1)
-    # order ties that matter
-    key = torch.where(contrib, tstar, torch.full_like(tstar, math.inf))
-    srt = torch.sort(key, dim=1, stable=True)
-    m = int(contrib.sum(1).max().item()) if contrib.numel() else 0
-    if m >= 2:
+    with torch.no_grad():
+        rho2, tstar = rho2.detach(), tstar.detach()
+        o_hat = prep["o_hat"].detach()
+        rgb = prep["rgb"].detach()
+        raw = o_hat.unsqueeze(0) * torch.exp(-0.5 * rho2)
+        a_raw = torch.clamp(raw, max=ALPHA_MAX)
+        contrib = live & (raw >= ALPHA_MIN) & (tstar >= view.znear)
+        touched = raw >= ALPHA_MIN * (1 - rel_alpha)
+        near_alpha = (raw - ALPHA_MIN).abs() < rel_alpha * ALPHA_MIN
+        near_z = ((tstar - view.znear).abs() < rel_t * view.znear) & touched
+        edge_g = (o_hat - ALPHA_MIN).abs() < rel_tau * ALPHA_MIN
+        if not eval2d:
+            uu = (prep["u_cam"].detach() ** 2).sum(-1)
+            tau = prep["tau"].detach()
+            edge_g = edge_g | ((uu - tau).abs() < rel_tau * tau.abs())
+        flip = ((near_alpha | near_z) & (live | edge_g.unsqueeze(0))) | (touched & edge_g.unsqueeze(0))
+        # transmittance in front of every Gaussian at its own depth
+        key = torch.where(contrib, tstar, torch.full_like(tstar, math.inf))
+        srt = torch.sort(key, dim=1, stable=True)
+        m = max(int(contrib.sum(1).max().item()) if contrib.numel() else 0, 1)
         order = srt.indices[:, :m]
-        t_s = srt.values[:, :m]
-        a_s = torch.clamp(torch.gather(raw, 1, order), max=ALPHA_MAX)
-        valid = torch.isfinite(t_s)
-        a_s = torch.where(valid, a_s, torch.zeros_like(a_s))
-        T_b = torch.cumprod(torch.cat([torch.ones_like(a_s[:, :1]), 1 - a_s[:, :-1]], 1), 1)
-        c_s = prep["rgb"][order]                                   # [P,m,3]
-        close = valid[:, 1:] & valid[:, :-1] & \
-            ((t_s[:, 1:] - t_s[:, :-1]) <= rel_t * t_s[:, :-1].abs())
-        effect = T_b[:, :-1] * a_s[:, :-1] * a_s[:, 1:] * \
-            (c_s[:, :-1, :] - c_s[:, 1:, :]).abs().amax(-1)
-        flag |= (close & (effect > swap)).any(1)
-    return flag
+        t_s = srt.values[:, :m].contiguous()
+        a_s = torch.where(torch.isfinite(t_s), torch.gather(a_raw, 1, order), torch.zeros_like(t_s))
+        T_b = torch.cumprod(torch.cat([torch.ones_like(a_s[:, :1]), 1 - a_s], 1), 1)   # [P, m+1]
+        pos = torch.searchsorted(t_s, tstar.contiguous(), side="left")                  # [P, G]
+        T_at = torch.gather(T_b, 1, pos)
+        c_g = rgb.amax(-1).unsqueeze(0)                                                  # [1, G]
+        bgmax = float(view.bg.max().item()) if view.bg.numel() else 0.0
+        cmax = torch.where(contrib | flip, c_g, torch.zeros_like(c_g)).amax(1)
+        cmax = torch.clamp(cmax, min=max(1.0, bgmax))                                    # [P]
+        effect = torch.where(flip, a_raw * T_at, torch.zeros_like(a_raw)).sum(1) * cmax
+        effect = effect + torch.where(flip.any(1), T_STOP * cmax, torch.zeros_like(cmax))
+        # near-tied adjacent contributors
+        if m >= 2:
+            valid = torch.isfinite(t_s)
+            c_s = rgb[order]                                                             # [P,m,3]
+            close = valid[:, 1:] & valid[:, :-1] & \
+                ((t_s[:, 1:] - t_s[:, :-1]) <= rel_t * t_s[:, :-1].abs())
+            sw = T_b[:, :m - 1] * a_s[:, :-1] * a_s[:, 1:] * \
+                (c_s[:, :-1, :] - c_s[:, 1:, :]).abs().amax(-1)
+            effect = effect + torch.where(close, sw, torch.zeros_like(sw)).sum(1)
+    return effect > budget

@@ -51,7 +51,7 @@ class aaag_stats(C.Structure):
     _fields_ = [("n_gaussians", C.c_uint64), ("n_visible", C.c_uint64), ("n_pairs", C.c_uint64),
                 ("pair_capacity", C.c_uint64), ("tiles_tested", C.c_uint64),
                 ("evaluations", C.c_uint64), ("blended", C.c_uint64), ("misorders", C.c_uint64),
-                ("replay_mismatch", C.c_uint64), ("capacity_overflow", C.c_uint32), ("timeout", C.c_uint32)]
+                ("extra_passes", C.c_uint64), ("replay_mismatch", C.c_uint64), ("capacity_overflow", C.c_uint32), ("timeout", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -100,6 +100,7 @@ SIGNATURES = [
                                   C.c_void_p, C.c_size_t, C.POINTER(C.c_int32), C.c_void_p]),
     ("aaag_radix_sort_static_capacity", C.c_int64, []),
     ("aaag_radix_sort_static", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
+    ("aaag_radix_sort_static_status", C.c_int, []),
     ("aaag_vhat_train", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     ("aaag_get_stats", C.c_int, [C.c_void_p, C.POINTER(aaag_stats), C.c_void_p]),
     ("aaag_last_error", C.c_char_p, []),
@@ -235,6 +236,12 @@ def aaag_radix_sort_static_capacity():
 
 def aaag_radix_sort_static(keys, vals, n, key_bits, stream):
     _check(lib().aaag_radix_sort_static(keys, vals, n, key_bits, stream), "aaag_radix_sort_static")
+
+
+def aaag_radix_sort_static_status():
+    """Status code of the last aaag_radix_sort_static on the current device
+    (0 = OK, 4 = a bounded wait gave up); call after synchronising its stream."""
+    return int(lib().aaag_radix_sort_static_status())
 
 
 def aaag_get_stats(ws, stream, check=True):

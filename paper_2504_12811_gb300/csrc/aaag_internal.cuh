@@ -29,6 +29,11 @@ __host__ __device__ constexpr int64_t sort_max_tiles(int64_t n) {
              : (n + 2047) / 2048;
 }
 constexpr int kMaxTileBits = 16;          // at most 65536 tiles per image
+// Ablations whose pairs are keyed by the view depth of the mean instead of a
+// lower bound of t*, and those of them that keep every key bit (their blend
+// order follows the pair order).
+constexpr uint32_t kMeanDepthKeyFlags = AAAG_FLAG_NO_RESORT | AAAG_FLAG_EVAL_2D | AAAG_FLAG_KBUFFER;
+constexpr uint32_t kFullKeyFlags = AAAG_FLAG_NO_RESORT | AAAG_FLAG_KBUFFER;
 
 // Frame constants, prepared on the host in double precision and rounded once.
 struct FrameConst {
@@ -84,12 +89,13 @@ enum StatSlot : int {
   kStatChunks = 11,        // chunks of 32 candidate tiles (K2 work items)
   kStatChunksClipped = 12, // uint32: chunk count clipped to the chunk capacity
   kStatPairsClipped = 13,  // uint32: pair count clipped to the pair capacity
-  kStatFrameReset = 14,    // slots below this one are cleared at the start of every frame
-  kStatReplayMismatch = 14,// pixels whose backward replay blended a different count
-  kStatBatchCounter = 15,  // uint32 work-item counter of the batched render
-  kStatSortEpoch = 16,
-  kStatFrameEpoch = 17,    // bumped by every frame's constants: tags the cull look-back words
-  kStatCount = 18
+  kStatExtraPasses = 14,   // depth-peeling passes beyond each pixel's first
+  kStatFrameReset = 15,    // slots below this one are cleared at the start of every frame
+  kStatReplayMismatch = 15,// pixels whose backward replay blended a different count
+  kStatBatchCounter = 16,  // uint32 work-item counter of the batched render
+  kStatSortEpoch = 17,
+  kStatFrameEpoch = 18,    // bumped by every frame's constants: tags the cull look-back words
+  kStatCount = 19
 };
 
 }  // namespace aaag
@@ -114,6 +120,7 @@ struct aaag_workspace {
   uint32_t* chunk_owner;         // [chunk_capacity] Gaussian of each chunk
   uint32_t* chunk_mask;          // [chunk_capacity] needed-tile ballot of each chunk
   unsigned long long* cull_lookback;   // look-back words of the cull's scans
+  int64_t n_cull_words;
   uint32_t* keys[2];
   uint32_t* vals[2];
   uint32_t* sort_hist;           // [4][256]
@@ -143,26 +150,42 @@ aaag_status check_launch(const char* what);
 // kernel launchers (one per translation unit)
 aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st);
-void prepare_cull_kernels();
 aaag_status launch_cull_wait_selftest(aaag_workspace* ws, cudaStream_t st);
-aaag_status launch_sort_wait_selftest(aaag_workspace* ws, cudaStream_t st);
+aaag_status launch_sort_wait_selftest(unsigned long long* lookback, unsigned long long* timeout_flag,
+                                      cudaStream_t st);
+aaag_status static_sort_wait_selftest(cudaStream_t st);
 int64_t cull_lookback_words(int64_t n, int64_t chunk_cap);
 aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st);
 aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, float* const* alpha, int n,
                                 cudaStream_t st);
-void prepare_render_kernels();
-void prepare_backward_kernels();
-void prepare_sort_kernels();
+// Launch shapes that depend on the device: its SM count and the occupancy of
+// the persistent kernels, queried once per device with that device current
+// (thread-safe; every launcher reads the current device's entry).
+struct LaunchConfig {
+  int sms;
+  int pre_per_sm;        // preprocess_kernel blocks per SM
+  int cull_a_per_sm;     // chunk_offsets_kernel
+  int cull_b_per_sm;     // cull_emit_kernel
+  int sort_pass_per_sm;  // sort_pass_kernel
+  int serve_per_sm;      // serve_render_kernel
+};
+const LaunchConfig& launch_config();
+// per translation unit: function attributes and occupancy of its kernels
+void configure_preprocess(LaunchConfig& c);
+void configure_cull(LaunchConfig& c);
+void configure_sort(LaunchConfig& c);
+void configure_render(LaunchConfig& c);
+void configure_backward(LaunchConfig& c);
 constexpr int kMaxRenderBatch = 64;
 aaag_status launch_render_backward(const SceneDev& s, aaag_workspace* ws, const float* rgb, const float* drgb,
                                    const float* dalpha, const aaag_grads* out, cudaStream_t st);
 aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                                 uint32_t* vals_alt, const uint32_t* n_dev, int64_t n_max,
                                 int key_bits, uint32_t* hist, uint32_t* counters,
-                                unsigned long long* lookback, unsigned long long* epoch,
-                                unsigned long long* timeout_flag, int* result_in_alt,
-                                cudaStream_t st, bool prepared = false);
+                                unsigned long long* lookback, int64_t lookback_words,
+                                unsigned long long* epoch, unsigned long long* timeout_flag,
+                                int* result_in_alt, cudaStream_t st, bool prepared = false);
 size_t radix_sort_scratch(int64_t n_max);
 
 // ---------------------------------------------------------------------------

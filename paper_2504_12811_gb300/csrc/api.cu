@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 
 #include "aaag_internal.cuh"
 
@@ -27,6 +28,29 @@ aaag_status check_launch(const char* what) {
     return AAAG_ERR_CUDA;
   }
   return AAAG_OK;
+}
+
+const LaunchConfig& launch_config() {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static LaunchConfig cfg[kMaxDevices];
+  static bool ready[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ready[dev]) {
+    LaunchConfig c;
+    std::memset(&c, 0, sizeof(c));
+    if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c.sms < 1) c.sms = 1;
+    configure_preprocess(c);
+    configure_cull(c);
+    configure_sort(c);
+    configure_render(c);
+    configure_backward(c);
+    cfg[dev] = c;
+    ready[dev] = true;
+  }
+  return cfg[dev];
 }
 
 namespace {
@@ -151,9 +175,10 @@ aaag_status make_frame(const aaag_camera* cam, const aaag_params* prm, int sh_de
   // key = tile id above the depth key: 24 bits (three radix passes) while at
   // least 16 depth bits remain, else 32.  Coarser depth keys put more pairs of
   // a tile under one key, where they arrive in index order: with 11 depth bits
-  // at 1080p the per-pixel queue overflowed 20-45% more often.  (Blending in
-  // pair order, the no-re-sort ablation keeps the full 32.)
-  const int key_bits = (bits + kMinDepthBits <= 24 && !(fc->flags & AAAG_FLAG_NO_RESORT)) ? 24 : 32;
+  // at 1080p the per-pixel queue overflowed 20-45% more often.  (The no-re-sort
+  // and bounded-buffer ablations, whose blend order follows the pair order,
+  // keep the full 32.)
+  const int key_bits = (bits + kMinDepthBits <= 24 && !(fc->flags & kFullKeyFlags)) ? 24 : 32;
   fc->tile_bits = bits;
   fc->depth_bits = key_bits - bits;
   // (bits(z) - bits(znear)) spans 2^27 for z/znear up to 2^16; larger depths
@@ -172,10 +197,20 @@ __global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
 // other kernel of the frame: a captured frame graph is re-aimed at a new
 // camera by updating this one node.
 // Frame constants to device memory; the frame epoch tags this frame's cull
-// look-back words.
-__global__ void set_frame_kernel(FrameConst* dst, FrameConst v, unsigned long long* frame_epoch) {
-  *dst = v;
-  *frame_epoch += 1ull;
+// look-back words with its low 24 bits.  When those wrap to zero every word is
+// cleared (an unpublished word), so that a word left from 2^24 frames earlier
+// can never pass for one of this frame.
+__global__ void set_frame_kernel(FrameConst* dst, FrameConst v, unsigned long long* frame_epoch,
+                                 unsigned long long* cull_lb, long long lb_words) {
+  __shared__ unsigned long long e;
+  if (threadIdx.x == 0) {
+    *dst = v;
+    e = *frame_epoch + 1ull;
+    *frame_epoch = e;
+  }
+  __syncthreads();
+  if ((e & 0xffffffull) == 0ull)
+    for (long long i = threadIdx.x; i < lb_words; i += blockDim.x) cull_lb[i] = 0ull;
 }
 
 SceneDev scene_dev(const aaag_scene* scene) {
@@ -288,20 +323,18 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
   w->grad_acc = reinterpret_cast<float4*>(b + L.grad);
   w->fc_dev = reinterpret_cast<FrameConst*>(b + L.fc);
   w->n_sort_tiles = sort_max_tiles(pair_capacity);
+  w->n_cull_words = cull_lookback_words(n, w->chunk_capacity);
   // the look-back epoch lives in the stats block and must start defined; the
   // look-back words are cleared once so that no stale word can match an epoch
   if (cudaMemset(w->stats, 0, kStatCount * 8) != cudaSuccess ||
       cudaMemset(w->sort_lookback, 0, (size_t)(w->n_sort_tiles + 1) * 256 * 8) != cudaSuccess ||
-      cudaMemset(w->cull_lookback, 0, (size_t)cull_lookback_words(n, w->chunk_capacity) * 8) != cudaSuccess) {
+      cudaMemset(w->cull_lookback, 0, (size_t)w->n_cull_words * 8) != cudaSuccess) {
     std::free(w);
     return check_launch("workspace_init memset");
   }
-  // function attributes and occupancy queries, once per process, outside any
+  // function attributes and occupancy queries of this device, outside any
   // stream capture
-  prepare_render_kernels();
-  prepare_backward_kernels();
-  prepare_sort_kernels();
-  prepare_cull_kernels();
+  launch_config();
   *ws = w;
   return AAAG_OK;
 }
@@ -373,7 +406,8 @@ aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, 
   ws->have_frame = true;
   ws->pairs_unsorted = false;
   ws->sorted_in_alt = 0;
-  set_frame_kernel<<<1, 1, 0, stream>>>(ws->fc_dev, fc, ws->stats + kStatFrameEpoch);
+  set_frame_kernel<<<1, 256, 0, stream>>>(ws->fc_dev, fc, ws->stats + kStatFrameEpoch, ws->cull_lookback,
+                                          (long long)ws->n_cull_words);
   e = check_launch("set_frame");
   if (e != AAAG_OK) return e;
   // reset per-frame statistics (keep the sort epoch)
@@ -482,8 +516,9 @@ aaag_status aaag_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, 
   unsigned long long* lookback = reinterpret_cast<unsigned long long*>(b + 4096 + 256);
   set_u32_kernel<<<1, 1, 0, stream>>>(n_dev, (uint32_t)n);
   int alt = 0;
+  const int64_t lb_words = std::max<int64_t>(sort_max_tiles(n), 1) * 256;
   const aaag_status e = radix_sort_device_n(keys, vals, keys_alt, vals_alt, n_dev, n, key_bits, hist, counters,
-                                            lookback, epoch, timeout, &alt, stream);
+                                            lookback, lb_words, epoch, timeout, &alt, stream);
   *result_in_alt = alt;
   return e;
 }
@@ -506,6 +541,7 @@ aaag_status aaag_get_stats(aaag_workspace* ws, aaag_stats* out, cudaStream_t str
   out->evaluations = h[kStatEvaluations];
   out->blended = h[kStatBlended];
   out->misorders = h[kStatMisorders];
+  out->extra_passes = h[kStatExtraPasses];
   out->capacity_overflow = (uint32_t)h[kStatOverflow];
   out->timeout = (uint32_t)h[kStatTimeout];
   out->replay_mismatch = h[kStatReplayMismatch];
@@ -660,7 +696,9 @@ aaag_status aaag_graph_launch(aaag_graph* g, const aaag_camera* camera, cudaStre
   if (e != AAAG_OK) return e;
   FrameConst* dst = ws->fc_dev;
   unsigned long long* epoch = ws->stats + kStatFrameEpoch;
-  void* args[3] = {&dst, &fc, &epoch};
+  unsigned long long* cull_lb = ws->cull_lookback;
+  long long lb_words = (long long)ws->n_cull_words;
+  void* args[5] = {&dst, &fc, &epoch, &cull_lb, &lb_words};
   cudaKernelNodeParams p = g->frame_params;
   p.kernelParams = args;
   p.extra = nullptr;
@@ -675,13 +713,15 @@ aaag_status aaag_graph_launch(aaag_graph* g, const aaag_camera* camera, cudaStre
 }
 
 aaag_status aaag_selftest_wait_timeout(aaag_workspace* ws, int32_t which, cudaStream_t stream) {
+  if (which == 2) return static_sort_wait_selftest(stream);
   if (!ws || which < 0 || which > 1) {
     set_error("aaag_selftest_wait_timeout: invalid argument");
     return AAAG_ERR_INVALID_ARG;
   }
   if (cudaMemsetAsync(ws->stats + kStatTimeout, 0, sizeof(unsigned long long), stream) != cudaSuccess)
     return check_launch("aaag_selftest_wait_timeout memset");
-  return which == 0 ? launch_cull_wait_selftest(ws, stream) : launch_sort_wait_selftest(ws, stream);
+  return which == 0 ? launch_cull_wait_selftest(ws, stream)
+                    : launch_sort_wait_selftest(ws->sort_lookback, ws->stats + kStatTimeout, stream);
 }
 
 void aaag_graph_destroy(aaag_graph* g) {

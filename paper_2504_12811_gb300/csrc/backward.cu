@@ -364,9 +364,9 @@ render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restr
   bl.Tfinal = Tf;
   bl.done = !in_image;
   unsigned long long neval = 0;
-  uint32_t nmis = 0;
+  uint32_t nmis = 0, npass = 0;
   __syncthreads();
-  traverse_tile<true>(s, ranges[tile], keys, vals, rec, aux, fc, tx, ty, bl.x, bl.y, bl, neval, nmis);
+  traverse_tile<true>(s, ranges[tile], keys, vals, rec, aux, fc, tx, ty, bl.x, bl.y, bl, neval, nmis, npass);
   // the replay must reproduce the forward blend count
   const bool mismatch = in_image && bl.nblend != n_blended[p];
   const unsigned ball = __ballot_sync(0xffffffffu, mismatch);
@@ -587,19 +587,16 @@ preprocess_backward_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const
 
 }  // namespace
 
-void prepare_backward_kernels() {
-  static bool done = false;
-  if (done) return;
+void configure_backward(LaunchConfig&) {
   cudaFuncSetAttribute(render_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kBackwardSmemBytes);
-  done = true;
 }
 
 aaag_status launch_render_backward(const SceneDev& s, aaag_workspace* ws, const float* rgb, const float* drgb,
                                    const float* dalpha, const aaag_grads* out, cudaStream_t st) {
   if (cudaMemsetAsync(ws->grad_acc, 0, (size_t)ws->n * sizeof(float4) * 4, st) != cudaSuccess)
     return check_launch("backward memset");
-  prepare_backward_kernels();
+  launch_config();   // function attributes of this device
   const int alt = ws->sorted_in_alt;
   render_backward_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kBackwardSmemBytes, st>>>(
       ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->aux, ws->fc_dev, rgb, drgb, dalpha, ws->final_T,

@@ -381,7 +381,7 @@ cull_emit_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
           const int txi = tx0 + j % nx, tyi = ty0 + j / nx;
           const uint32_t t = (uint32_t)(tyi * fc.tiles_x + txi);
           uint32_t dk = aw;
-          if (!(fc.flags & (AAAG_FLAG_NO_RESORT | AAAG_FLAG_EVAL_2D))) {
+          if (!(fc.flags & kMeanDepthKeyFlags)) {
             const float4* r = reinterpret_cast<const float4*>(rec + gi);
             dk = max(dk, tile_depth_key(__ldg(r + 0), __ldg(r + 1), __ldg(r + 2), fc, txi, tyi));
           }
@@ -394,24 +394,15 @@ cull_emit_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
   }
 }
 
-int g_sms = 0;
-int g_blocks_a = 0, g_blocks_b = 0;
-
-void init_cull_occupancy() {
-  if (g_sms) return;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-  if (g_sms < 1) g_sms = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_blocks_a, chunk_offsets_kernel, kThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_blocks_b, cull_emit_kernel, kThreads, 0);
-  g_blocks_a = std::max(1, g_blocks_a);
-  g_blocks_b = std::max(1, g_blocks_b);
-}
-
 }  // namespace
 
-void prepare_cull_kernels() { init_cull_occupancy(); }
+void configure_cull(LaunchConfig& c) {
+  int a = 1, b = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, chunk_offsets_kernel, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cull_emit_kernel, kThreads, 0);
+  c.cull_a_per_sm = std::max(1, a);
+  c.cull_b_per_sm = std::max(1, b);
+}
 
 aaag_status launch_cull_wait_selftest(aaag_workspace* ws, cudaStream_t st) {
   cull_wait_selftest_kernel<<<1, 32, 0, st>>>(ws->cull_lookback, ws->stats + kStatTimeout);
@@ -423,27 +414,27 @@ int64_t cull_lookback_words(int64_t n, int64_t chunk_cap) {
 }
 
 aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st) {
-  init_cull_occupancy();
+  const LaunchConfig& lc = launch_config();
   const int64_t n = ws->n;
   uint32_t* n_chunks = reinterpret_cast<uint32_t*>(ws->stats + kStatChunksClipped);
   uint32_t* n_pairs = reinterpret_cast<uint32_t*>(ws->stats + kStatPairsClipped);
   unsigned long long* look_a = ws->cull_lookback;
   unsigned long long* look_b = ws->cull_lookback + (ws->n_max + kOffTile - 1) / kOffTile + 1;
   const int64_t tiles_a = std::max<int64_t>((n + kOffTile - 1) / kOffTile, 1);
-  const unsigned grid_a = (unsigned)std::min<int64_t>(tiles_a, (int64_t)g_sms * g_blocks_a);
+  const unsigned grid_a = (unsigned)std::min<int64_t>(tiles_a, (int64_t)lc.sms * lc.cull_a_per_sm);
   chunk_offsets_kernel<<<grid_a, kThreads, 0, st>>>(ws->counts, n, ws->chunk_capacity, ws->offsets,
                                                     ws->chunk_owner, look_a, ws->stats, n_chunks, ws->sort_hist,
                                                     ws->sort_counters);
   aaag_status e = check_launch("chunk_offsets");
   if (e != AAAG_OK) return e;
   const unsigned grid_t = (unsigned)std::max<int64_t>(
-      std::min<int64_t>((ws->chunk_capacity + kWarps - 1) / kWarps, (int64_t)g_sms * 16), 1);
+      std::min<int64_t>((ws->chunk_capacity + kWarps - 1) / kWarps, (int64_t)lc.sms * 16), 1);
   cull_test_kernel<<<grid_t, kThreads, 0, st>>>(ws->records, ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets,
                                                 n_chunks, ws->chunk_capacity, ws->chunk_mask, ws->stats);
   e = check_launch("cull_test");
   if (e != AAAG_OK) return e;
   const int64_t tiles_b = std::max<int64_t>((ws->chunk_capacity + kChunkTile - 1) / kChunkTile, 1);
-  const unsigned grid_b = (unsigned)std::min<int64_t>(tiles_b, (int64_t)g_sms * g_blocks_b);
+  const unsigned grid_b = (unsigned)std::min<int64_t>(tiles_b, (int64_t)lc.sms * lc.cull_b_per_sm);
   cull_emit_kernel<<<grid_b, kThreads, 0, st>>>(ws->records, ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets, n_chunks,
                                                 ws->chunk_capacity, ws->chunk_mask, ws->keys[0], ws->vals[0],
                                                 ws->capacity, look_b, ws->stats, n_pairs);

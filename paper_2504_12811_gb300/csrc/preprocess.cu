@@ -420,8 +420,8 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev& s, const FrameCon
       const float3 A3p = A3 - a3c * ch;
       float t_lo = vz - sqrtf(tau_c * dot3(A3p, A3p)) + fminf(a3c, 0.0f) * tau_c / cn;
       t_lo -= 1e-5f * fabsf(t_lo) + 1e-6f;
-      // (sort and 2D-evaluation ablations: the depth of the mean)
-      const float zk = (fc.flags & (AAAG_FLAG_NO_RESORT | AAAG_FLAG_EVAL_2D)) ? fmaxf(vz, fc.znear)
+      // (sort, bounded-buffer and 2D-evaluation ablations: the depth of the mean)
+      const float zk = (fc.flags & kMeanDepthKeyFlags) ? fmaxf(vz, fc.znear)
                                                                              : fmaxf(fmaxf(t_lo, z_lo), fc.znear);
       uint32_t dk = (__float_as_uint(zk) - fc.znear_bits) >> fc.depth_shift;
       const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
@@ -509,19 +509,18 @@ preprocess_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const uint32_t
   if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(&stats[kStatVisible], (unsigned long long)nvis);
 }
 
-int g_pre_blocks = 0;
-
 }  // namespace
+
+void configure_preprocess(LaunchConfig& c) {
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, preprocess_kernel, 256, 0);
+  c.pre_per_sm = std::max(1, per_sm);
+}
 
 aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_t st) {
   if (s.n == 0) return AAAG_OK;
-  if (!g_pre_blocks) {
-    int dev = 0, sms = 1, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, preprocess_kernel, 256, 0);
-    g_pre_blocks = std::max(1, sms) * std::max(1, per_sm);
-  }
+  const LaunchConfig& lc = launch_config();
+  const int64_t pre_blocks = (int64_t)lc.sms * lc.pre_per_sm;
   const int threads = 256;
   const int64_t blocks = (s.n + threads - 1) / threads;
   const int64_t tblocks = ((s.n + 3) / 4 + threads - 1) / threads;
@@ -533,7 +532,7 @@ aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_
                                                                 vec4);
   aaag_status e = check_launch("preprocess_test");
   if (e != AAAG_OK) return e;
-  const unsigned grid = (unsigned)std::min<int64_t>(blocks, g_pre_blocks);
+  const unsigned grid = (unsigned)std::min<int64_t>(blocks, pre_blocks);
   preprocess_kernel<<<grid, threads, 0, st>>>(s, ws->fc_dev, ws->candidates, n_cand, ws->records, ws->aux,
                                               ws->counts, ws->stats);
   return check_launch("preprocess");

@@ -9,12 +9,13 @@
 // affine 3-vectors, two dot products, one reciprocal and one exp2.
 //
 // Per-pixel ordering: contributors (alpha >= 1/255, t* >= znear) enter a
-// register queue sorted by (t*, arrival).  Pairs arrive with non-decreasing
-// key L, a lower bound of the t* of every later contributor, so a queued
-// entry with t* < L can never be overtaken and is blended at once.  Only when
-// the queue is full is an entry released early (counted as a potential
-// misorder).  Blending stops before the contributor that would take
-// transmittance below 1e-4.
+// queue sorted by (t*, arrival).  Pairs arrive with non-decreasing key L, a
+// lower bound of the t* of every later contributor, so a queued entry with
+// t* < L can never be overtaken and is blended at once.  When the queue is
+// full, the farthest contributors are deferred to another pass over the tile
+// (depth peeling), so the order is exact; only the bounded-buffer ablation
+// releases entries early (counted as potential misorders).  Blending stops
+// before the contributor that would take transmittance below 1e-4.
 #include <algorithm>
 #include <cstring>
 
@@ -75,9 +76,9 @@ __device__ __forceinline__ void render_tile(TileSmem<IndexQueue>& s, int tile, c
   bl.done = !in_image;
   bl.nblend = 0;
   unsigned long long neval = 0;
-  uint32_t nmis = 0;
+  uint32_t nmis = 0, npass = 0;
   traverse_tile<false>(s, ranges[tile], keys, vals, rec, aux, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f, bl,
-                       neval, nmis);
+                       neval, nmis, npass);
 
   if (in_image) {
     const size_t HW = (size_t)fc.W * fc.H;
@@ -89,17 +90,19 @@ __device__ __forceinline__ void render_tile(TileSmem<IndexQueue>& s, int tile, c
     final_T[p] = bl.T;
     n_blended[p] = bl.nblend;
   }
-  unsigned long long e = neval, b = bl.nblend, m = nmis;
+  unsigned long long e = neval, b = bl.nblend, m = nmis, x = npass;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     e += __shfl_xor_sync(0xffffffffu, e, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
     m += __shfl_xor_sync(0xffffffffu, m, o);
+    x += __shfl_xor_sync(0xffffffffu, x, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (e) atomicAdd(&stats[kStatEvaluations], e);
     if (b) atomicAdd(&stats[kStatBlended], b);
     if (m) atomicAdd(&stats[kStatMisorders], m);
+    if (x) atomicAdd(&stats[kStatExtraPasses], x);
   }
 }
 
@@ -160,26 +163,19 @@ serve_render_kernel(const __grid_constant__ RenderBatch b, uint32_t* __restrict_
   }
 }
 
-int g_serve_blocks = 0;
-
 }  // namespace
 
-void prepare_render_kernels() {
-  static bool done = false;
-  if (done) return;
+void configure_render(LaunchConfig& c) {
   cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kForwardSmemBytes);
   cudaFuncSetAttribute(serve_render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kForwardSmemBytes);
-  int dev = 0, sms = 1, per_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_render_kernel, kTilePixels, kForwardSmemBytes);
-  g_serve_blocks = std::max(1, sms) * std::max(1, per_sm);
-  done = true;
+  c.serve_per_sm = std::max(1, per_sm);
 }
 
 aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, float* const* alpha, int n,
                                 cudaStream_t st) {
-  prepare_render_kernels();
+  const LaunchConfig& lc = launch_config();
   RenderBatch b;
   std::memset(&b, 0, sizeof(b));
   uint32_t total = 0;
@@ -206,13 +202,13 @@ aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, fl
   b.total = total;
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws[0]->stats + kStatBatchCounter);
   if (cudaMemsetAsync(counter, 0, 4, st) != cudaSuccess) return check_launch("render_batch memset");
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g_serve_blocks, total));
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)lc.sms * lc.serve_per_sm, total));
   serve_render_kernel<<<grid, kTilePixels, kForwardSmemBytes, st>>>(b, counter);
   return check_launch("serve_render");
 }
 
 aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st) {
-  prepare_render_kernels();
+  launch_config();   // function attributes of this device
   const int alt = ws->sorted_in_alt;
   render_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kForwardSmemBytes, st>>>(ws->ranges, ws->keys[alt], ws->vals[alt],
                                                                ws->records, ws->aux, ws->fc_dev, rgb, alpha, ws->final_T,

@@ -26,9 +26,23 @@
 //   2. if t < L_{k+1} the new contributor is blended at once, followed by the
 //      queued entries below L_{k+1}: nothing later can precede any of them;
 //   3. otherwise it is inserted into the pixel's sorted queue.
-// The result is the exact (t*, arrival) order as long as the queue does not
-// overflow; on overflow the nearer of the queue front and the new entry is
-// blended early and counted as a potential misorder.  Queue entries stay in
+// This is the exact (t*, arrival) order while the queue has room.  When it is
+// full, the order stays exact by depth peeling: a pass blends only the
+// contributors with lo <= t* < hi.  The queue keeps the nearest ones; the
+// farther of the new entry and the queue's last entry is deferred, hi drops
+// to its depth, and every queued entry at or beyond hi leaves too.  Once
+// L_{k+1} >= hi nothing later can fall inside the window, so the pixel drains
+// its queue and closes the pass.  A pixel that deferred anything runs another
+// pass over its tile with lo = hi, starting at the first pair that inserted
+// into its queue after it was last empty before the first deferral (every
+// deferred contributor arrived there or later; everything before it was
+// blended).  Each pass blends its window completely, in order, so the
+// passes together blend exactly the plain (t*, arrival) sequence.  When the
+// queue is full and its nearest entry lies at lo itself, that entry is
+// released at once instead (nothing this pass can precede it), so hi > lo and
+// every pass advances.  The bounded-buffer ablation (AAAG_FLAG_KBUFFER)
+// keeps the approximate rule: a full queue releases its nearest entry early.
+// Queue entries stay in
 // fixed per-thread slots in shared memory, laid out [slot][thread] (bank-
 // conflict free); their order lives in one 64-bit register holding the slot
 // numbers nearest first, 4 bits each, so an insertion moves no entry (a scan
@@ -61,6 +75,7 @@ struct StageSmem {
   float4 f[kTilePixels];    // Dy.xyz, G.z
   float L[kTilePixels];     // L_next: lower bound of t* for every later pair
   uint32_t gid[kTilePixels];  // Gaussian index
+  uint32_t start;           // first pair of the next depth-peeling pass
 };
 
 // Queue store, [slot][thread], one array per field: (t*, alpha, Gaussian
@@ -184,6 +199,18 @@ struct SmemQueue {
     pop(a, p);
     bl.blend(a, p);
   }
+  // t* of the farthest entry (n > 0)
+  __device__ __forceinline__ float back_t() const { return q->t(slot_at(n - 1), tid); }
+  // remove every entry with t* >= h from the far end (deferred to a later pass)
+  __device__ __forceinline__ void drop_from(float h) {
+    while (n > 0) {
+      const int s = slot_at(n - 1);
+      if (q->t(s, tid) < h) break;
+      used &= ~(1u << s);
+      order &= ~(15ull << (4 * (n - 1)));
+      --n;
+    }
+  }
   // sorted insert (n < kQueue), after every entry with an equal t*
   __device__ __forceinline__ void insert(float t, float a, typename Q::Payload p) {
     int i = n;
@@ -238,12 +265,14 @@ __device__ __forceinline__ void release_rounds(SmemQueue<Q>& q, Blender& bl, Wan
 //   void end_item(int k);                            warp-converged, after item k
 //   void end_batch(uint32_t b0, int cnt);            block-converged, after a batch
 // The arithmetic, and so every blend decision, is the same either way.
+// npass counts this pixel's passes beyond the first (depth peeling); nmis the
+// early releases of the bounded-buffer ablation.
 template <bool CONVERGENT, class Blender>
 __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>& sm, const uint2 range, const uint32_t* __restrict__ keys,
                                               const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
                                               const uint4* __restrict__ aux, const FrameConst& fc, int tile_x,
                                               int tile_y, float x, float y, Blender& bl,
-                                              unsigned long long& neval, uint32_t& nmis) {
+                                              unsigned long long& neval, uint32_t& nmis, uint32_t& npass) {
   const int ox = tile_x * kTile, oy = tile_y * kTile;
   const float cxm = fc.cx - (float)ox, cym = fc.cy - (float)oy;
   const uint32_t wbit = 1u << (threadIdx.x >> 5);
@@ -251,125 +280,174 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
   // buffer is full (no release by key)
   const bool resort = !(fc.flags & AAAG_FLAG_NO_RESORT);
   const bool by_key = !(fc.flags & AAAG_FLAG_KBUFFER);
+  const bool peel = resort && by_key;   // exact order: defer instead of releasing early
   const float kInf = __int_as_float(0x7f800000);
+  constexpr uint32_t kNone = 0xffffffffu;
   StageSmem& s = sm.st;
   SmemQueue<typename Blender::Queue> q;
   q.q = &sm.q;
   q.tid = threadIdx.x;
-  q.n = 0;
-  q.order = 0ull;
-  q.used = 0u;
   q.ft = 0.0f;
-  for (uint32_t b0 = range.x; b0 < range.y; b0 += kTilePixels) {
-    if (__syncthreads_count(bl.done) == kTilePixels) break;
-    const uint32_t j = b0 + threadIdx.x;
-    if (j < range.y) {
-      const float Lnext = j + 1 < range.y ? decode_depth(keys[j + 1], fc) : kInf;
-      const uint32_t gid = vals[j];
-      const uint4 ax = __ldg(aux + gid);
-      stage_one(s, threadIdx.x, rec, gid, make_uint2(ax.x, ax.y), Lnext, fc, cxm, cym, ox, oy);
-    }
-    __syncthreads();
-    const int cnt = (int)min((uint32_t)kTilePixels, range.y - b0);
-    bl.begin_batch(b0, cnt);
-    if (CONVERGENT || !bl.done) {
-      for (int k = 0; k < cnt; ++k) {
-        const float4 bq = s.b[k];
-        if (!(__float_as_uint(bq.w) & wbit)) continue;   // warp-uniform
-        if constexpr (CONVERGENT) {
-          // the same decisions as below, with the releases taken out of the
-          // per-lane branches into warp-wide rounds
-          bool contrib = false;
-          float ts = 0.0f, ca = 0.0f, Lnext = 0.0f;
-          EvalState ev{k, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-          if (!bl.done) {
-            ++neval;
-            const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
-            const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
-            const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
-            const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
-            const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
-            const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
-            const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
-            const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
-            const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
-            if (nn <= c.w * dd) {
-              const float inv = __fdividef(1.0f, dd);
-              const float rho2 = nn * inv;
-              const float raw = a.w * __expf(-0.5f * rho2);
-              const float t = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
-              if (raw >= kAlphaMin && t >= fc.znear) {
-                contrib = true;
-                ts = t;
-                ca = fminf(raw, kAlphaMax);
-                Lnext = by_key ? s.L[k] : -kInf;
-                ev = EvalState{k, n0, n1, n2, d0, d1, d2, inv, rho2};
+  float lo = -kInf;              // this pass blends contributors with lo <= t* < hi
+  uint32_t jfirst = range.x;     // earlier pairs hold nothing for this pixel's pass
+  bool more = !bl.done;          // this pixel takes part in the pass
+  uint32_t start = range.x;
+  for (;;) {
+    float hi = kInf;
+    bool open = more;
+    uint32_t jnext = kNone;      // where the next pass can start for this pixel
+    uint32_t jfill = range.x;    // pair that last inserted into an empty queue
+    q.n = 0;
+    q.order = 0ull;
+    q.used = 0u;
+    for (uint32_t b0 = start; b0 < range.y; b0 += kTilePixels) {
+      if constexpr (!CONVERGENT) {
+        // close the pass once no pair from here on can hold a contributor below hi
+        if (open && hi < kInf && decode_depth(keys[b0], fc) >= hi) {
+          while (q.n > 0 && !bl.done) q.release(bl);
+          open = false;
+        }
+      }
+      if (__syncthreads_count(open && !bl.done) == 0) break;
+      const uint32_t j = b0 + threadIdx.x;
+      if (j < range.y) {
+        const float Lnext = j + 1 < range.y ? decode_depth(keys[j + 1], fc) : kInf;
+        const uint32_t gid = vals[j];
+        const uint4 ax = __ldg(aux + gid);
+        stage_one(s, threadIdx.x, rec, gid, make_uint2(ax.x, ax.y), Lnext, fc, cxm, cym, ox, oy);
+      }
+      __syncthreads();
+      const int cnt = (int)min((uint32_t)kTilePixels, range.y - b0);
+      bl.begin_batch(b0, cnt);
+      if constexpr (CONVERGENT) {
+        for (int k = 0; k < cnt; ++k) {
+          const float4 bq = s.b[k];
+          const uint32_t jk = b0 + (uint32_t)k;
+          if (__float_as_uint(bq.w) & wbit) {   // warp-uniform
+            // the same decisions as the per-lane loop below, with the releases
+            // taken out of the per-lane branches into warp-wide rounds
+            bool contrib = false;
+            float ts = 0.0f, ca = 0.0f, Lnext = 0.0f;
+            EvalState ev{k, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            if (open && !bl.done && jk >= jfirst) {
+              ++neval;
+              const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
+              const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
+              const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
+              const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
+              const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
+              const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
+              const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
+              const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
+              const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+              if (nn <= c.w * dd) {
+                const float inv = __fdividef(1.0f, dd);
+                const float rho2 = nn * inv;
+                const float raw = a.w * __expf(-0.5f * rho2);
+                const float t = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
+                if (raw >= kAlphaMin && t >= fc.znear && t >= lo && t < hi) {
+                  contrib = true;
+                  ts = t;
+                  ca = fminf(raw, kAlphaMax);
+                  Lnext = by_key ? s.L[k] : -kInf;
+                  ev = EvalState{k, n0, n1, n2, d0, d1, d2, inv, rho2};
+                }
               }
             }
-          }
-          // 1. queued entries in front of the new one that nothing later can precede
-          release_rounds(q, bl, [&] { return contrib && q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext; });
-          const bool live = contrib && !bl.done;
-          const bool imm = live && (ts < Lnext || !resort);
-          bool ins = live && !imm;
-          // 2. the new contributor, then the rest below L_next; 3. queue it,
-          // and when the queue is full release the nearer of the front and the
-          // new entry early (a potential misorder).  The lanes of 2 and 3 are
-          // disjoint, so their releases share rounds.
-          if (imm) bl.blend_new(ca, ev);
-          bool early = false;
-          if (ins && q.n == kQueue) {
-            ++nmis;
-            if (ts < q.ft) {
-              bl.blend_new(ca, ev);
-              ins = false;
-            } else {
-              early = true;
+            // 1. queued entries in front of the new one that nothing later can precede
+            release_rounds(q, bl, [&] { return contrib && q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext; });
+            const bool live = contrib && !bl.done;
+            const bool imm = live && (ts < Lnext || !resort);
+            bool ins = live && !imm;
+            // 2. the new contributor, then the rest below L_next; 3. queue it.
+            // A full queue defers the farther of the new entry and its last
+            // one to a later pass (exact), or, in the bounded-buffer ablation
+            // or when its nearest entry lies at lo, releases the nearer of its
+            // front and the new entry.  The lanes of 2 and 3 are disjoint, so
+            // their releases share rounds.
+            if (imm) bl.blend_new(ca, ev);
+            bool early = false;
+            if (ins && q.n == kQueue) {
+              if (peel && q.ft > lo) {
+                if (jnext == kNone) jnext = jfill;
+                hi = fmaxf(ts, q.back_t());
+                q.drop_from(hi);
+                ins = ts < hi;
+              } else {
+                if (!peel) ++nmis;
+                if (ts < q.ft) {
+                  bl.blend_new(ca, ev);
+                  ins = false;
+                } else {
+                  early = true;
+                }
+              }
             }
+            release_rounds(q, bl, [&] {
+              const bool e = early;
+              early = false;
+              return e || (imm && q.n > 0 && !bl.done && q.ft < Lnext);
+            });
+            if (ins && !bl.done) {
+              if (q.n == 0) jfill = jk;
+              q.insert(ts, ca, bl.payload(k));
+            }
+            bl.end_item(k);
           }
-          release_rounds(q, bl, [&] {
-            const bool e = early;
-            early = false;
-            return e || (imm && q.n > 0 && !bl.done && q.ft < Lnext);
-          });
-          if (ins && !bl.done) q.insert(ts, ca, bl.payload(k));
-          bl.end_item(k);
-          if (__all_sync(0xffffffffu, bl.done)) break;   // warp-uniform
-        } else {
-          if (!bl.done) {
-            ++neval;
-            const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
-            const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
-            const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
-            const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
-            const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
-            const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
-            const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
-            const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
-            const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
-            // rho^2 > tau+ rules out alpha >= 1/255 without a division
-            if (nn <= c.w * dd) {
-              const float inv = __fdividef(1.0f, dd);
-              const float rho2 = nn * inv;
-              const float raw = a.w * __expf(-0.5f * rho2);
-              const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
-              if (raw >= kAlphaMin && ts >= fc.znear) {
-                const float Lnext = by_key ? s.L[k] : -kInf;
-                const float ca = fminf(raw, kAlphaMax);
-                const EvalState ev{k, n0, n1, n2, d0, d1, d2, inv, rho2};
-                // 1. queued entries in front of the new one that nothing later can precede
-                while (q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext) q.release(bl);
-                if (!bl.done) {
-                  if (ts < Lnext || !resort) {
-                    // 2. the new contributor, then the rest below L_next
-                    bl.blend_new(ca, ev);
-                    while (q.n > 0 && !bl.done && q.ft < Lnext) q.release(bl);
-                  } else {
-                    // 3. queue it; when full, release the nearer of the front and
-                    // the new entry early (a potential misorder)
-                    bool insert = true;
-                    if (q.n == kQueue) {
-                      ++nmis;
+          // close the pass once no later pair can hold a contributor below hi
+          const bool close = open && !bl.done && hi < kInf && s.L[k] >= hi;
+          release_rounds(q, bl, [&] { return close && q.n > 0 && !bl.done; });
+          if (close) open = false;
+          if (__all_sync(0xffffffffu, !open || bl.done)) break;   // warp-uniform
+        }
+        bl.end_batch(b0, cnt);
+      } else if (open && !bl.done) {
+        // pairs before jfirst hold nothing for this pass of this pixel
+        const int k0 = jfirst > b0 ? (int)min((uint32_t)cnt, jfirst - b0) : 0;
+        for (int k = k0; k < cnt; ++k) {
+          const float4 bq = s.b[k];
+          if (!(__float_as_uint(bq.w) & wbit)) continue;   // warp-uniform
+          ++neval;
+          const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
+          const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
+          const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
+          const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
+          const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
+          const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
+          const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
+          const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
+          const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+          // rho^2 > tau+ rules out alpha >= 1/255 without a division
+          if (nn <= c.w * dd) {
+            const float inv = __fdividef(1.0f, dd);
+            const float rho2 = nn * inv;
+            const float raw = a.w * __expf(-0.5f * rho2);
+            const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
+            if (raw >= kAlphaMin && ts >= fc.znear && ts >= lo && ts < hi) {
+              const float Lnext = by_key ? s.L[k] : -kInf;
+              const float ca = fminf(raw, kAlphaMax);
+              const EvalState ev{k, n0, n1, n2, d0, d1, d2, inv, rho2};
+              // 1. queued entries in front of the new one that nothing later can precede
+              while (q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext) q.release(bl);
+              if (!bl.done) {
+                if (ts < Lnext || !resort) {
+                  // 2. the new contributor, then the rest below L_next
+                  bl.blend_new(ca, ev);
+                  while (q.n > 0 && !bl.done && q.ft < Lnext) q.release(bl);
+                } else {
+                  // 3. queue it.  A full queue defers the farther of the new
+                  // entry and its last one to a later pass; in the
+                  // bounded-buffer ablation, or when its nearest entry lies at
+                  // lo, it releases the nearer of its front and the new entry
+                  bool insert = true;
+                  if (q.n == kQueue) {
+                    if (peel && q.ft > lo) {
+                      if (jnext == kNone) jnext = jfill;
+                      hi = fmaxf(ts, q.back_t());
+                      q.drop_from(hi);
+                      insert = ts < hi;
+                    } else {
+                      if (!peel) ++nmis;
                       if (ts < q.ft) {
                         bl.blend_new(ca, ev);
                         insert = false;
@@ -377,8 +455,17 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
                         q.release(bl);
                       }
                     }
-                    if (insert && !bl.done) q.insert(ts, ca, bl.payload(k));
                   }
+                  if (insert && !bl.done) {
+                    if (q.n == 0) jfill = b0 + (uint32_t)k;
+                    q.insert(ts, ca, bl.payload(k));
+                  }
+                }
+                // close the pass once no later pair can hold a contributor below hi
+                if (Lnext >= hi) {
+                  while (q.n > 0 && !bl.done) q.release(bl);
+                  open = false;
+                  break;
                 }
               }
             }
@@ -386,14 +473,25 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
           if (bl.done) break;
         }
       }
+      __syncthreads();
     }
-    if constexpr (CONVERGENT) bl.end_batch(b0, cnt);
+    if constexpr (CONVERGENT) {
+      release_rounds(q, bl, [&] { return q.n > 0 && !bl.done; });
+    } else {
+      while (q.n > 0 && !bl.done) q.release(bl);
+    }
+    // another pass for the pixels that deferred contributors
+    more = more && !bl.done && hi < kInf;
+    if (threadIdx.x == 0) s.start = kNone;
+    if (__syncthreads_count(more) == 0) break;
+    if (more) {
+      lo = hi;
+      jfirst = jnext;
+      ++npass;
+      atomicMin(&s.start, jnext);
+    }
     __syncthreads();
-  }
-  if constexpr (CONVERGENT) {
-    release_rounds(q, bl, [&] { return q.n > 0 && !bl.done; });
-  } else {
-    while (q.n > 0 && !bl.done) q.release(bl);
+    start = s.start;
   }
 }
 

@@ -11,10 +11,13 @@
 // block waits on belongs to a block that is already running.
 //
 // Look-back words are 64-bit: (epoch << 32) | (flag << 30) | count.  The epoch
-// (a device counter bumped by every sort, times 8 plus the pass) marks a word
-// as written by the current pass, so the look-back buffer never needs
-// clearing.  Every wait is bounded in time; on expiry the block sets a
-// timeout flag, proceeds with what it has and the frame is reported invalid.
+// (a device counter bumped by every sort, times 8 plus the pass, 32 bits) marks
+// a word as written by the current pass, so the look-back buffer needs no
+// clearing between sorts; only when the counter starts a new cycle of 2^29
+// sorts does the histogram kernel clear every word, so that a word written
+// 2^29 sorts earlier cannot pass for one of this sort.  Every wait is bounded
+// in time; on expiry the block sets a timeout flag, proceeds with what it has
+// and the frame is reported invalid.
 #include <algorithm>
 #include <utility>
 
@@ -44,8 +47,15 @@ __global__ void sort_init_kernel(uint32_t* hist, uint32_t* counters, unsigned lo
 
 __global__ void __launch_bounds__(256)
 sort_histogram_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev,
-                      int64_t n_max, int passes, uint32_t* __restrict__ hist) {
+                      int64_t n_max, int passes, uint32_t* __restrict__ hist,
+                      unsigned long long* __restrict__ lookback, int64_t lb_words,
+                      const unsigned long long* __restrict__ epoch) {
   __shared__ uint32_t sh[4][kRadix];
+  // a new cycle of look-back tags: clear every word (the passes come later)
+  if ((*epoch & ((1ull << 29) - 1ull)) == 0ull)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lb_words;
+         i += (int64_t)gridDim.x * blockDim.x)
+      lookback[i] = 0ull;
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
   const int64_t n = min((int64_t)*n_dev, n_max);
@@ -282,22 +292,13 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t*
   }
 }
 
-int g_sm_count = 0;
-int g_pass_blocks_per_sm = 0;
-
-void init_occupancy() {
-  if (g_sm_count) return;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pass_blocks_per_sm, sort_pass_kernel, kSortThreads, 0);
-  if (g_pass_blocks_per_sm < 1) g_pass_blocks_per_sm = 1;
-  if (g_sm_count < 1) g_sm_count = 1;
-}
-
 }  // namespace
 
-void prepare_sort_kernels() { init_occupancy(); }
+void configure_sort(LaunchConfig& c) {
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_pass_kernel, kSortThreads, 0);
+  c.sort_pass_per_sm = std::max(1, per_sm);
+}
 
 size_t radix_sort_scratch(int64_t n_max) {
   const int64_t tiles = sort_max_tiles(n_max);
@@ -308,22 +309,23 @@ size_t radix_sort_scratch(int64_t n_max) {
 aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                                 uint32_t* vals_alt, const uint32_t* n_dev, int64_t n_max,
                                 int key_bits, uint32_t* hist, uint32_t* counters,
-                                unsigned long long* lookback, unsigned long long* epoch,
-                                unsigned long long* timeout_flag, int* result_in_alt,
-                                cudaStream_t st, bool prepared) {
+                                unsigned long long* lookback, int64_t lookback_words,
+                                unsigned long long* epoch, unsigned long long* timeout_flag,
+                                int* result_in_alt, cudaStream_t st, bool prepared) {
   const int passes = (key_bits + 7) / 8;
   *result_in_alt = passes & 1;
   if (n_max <= 0 || passes == 0) {
     *result_in_alt = 0;
     return AAAG_OK;
   }
-  init_occupancy();
+  const LaunchConfig& lc = launch_config();
   if (!prepared) sort_init_kernel<<<1, 256, 0, st>>>(hist, counters, epoch);
-  const int64_t hblocks = std::min<int64_t>((n_max + 4095) / 4096, (int64_t)g_sm_count * 4);
-  sort_histogram_kernel<<<(unsigned)hblocks, 256, 0, st>>>(keys, n_dev, n_max, passes, hist);
+  const int64_t hblocks = std::min<int64_t>((n_max + 4095) / 4096, (int64_t)lc.sms * 4);
+  sort_histogram_kernel<<<(unsigned)hblocks, 256, 0, st>>>(keys, n_dev, n_max, passes, hist, lookback,
+                                                           lookback_words, epoch);
   aaag_status e = check_launch("sort_histogram");
   if (e != AAAG_OK) return e;
-  const int64_t grid = std::min<int64_t>(sort_max_tiles(n_max), (int64_t)g_sm_count * g_pass_blocks_per_sm);
+  const int64_t grid = std::min<int64_t>(sort_max_tiles(n_max), (int64_t)lc.sms * lc.sort_pass_per_sm);
   uint32_t* kin = keys;
   uint32_t* vin = vals;
   uint32_t* kout = keys_alt;
@@ -339,8 +341,9 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
   return AAAG_OK;
 }
 
-aaag_status launch_sort_wait_selftest(aaag_workspace* ws, cudaStream_t st) {
-  sort_wait_selftest_kernel<<<1, kRadix, 0, st>>>(ws->sort_lookback, ws->stats + kStatTimeout);
+aaag_status launch_sort_wait_selftest(unsigned long long* lookback, unsigned long long* timeout_flag,
+                                      cudaStream_t st) {
+  sort_wait_selftest_kernel<<<1, kRadix, 0, st>>>(lookback, timeout_flag);
   return check_launch("sort wait self-test");
 }
 
@@ -352,13 +355,12 @@ aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st) {
   const int key_bits = ws->fc.tile_bits + ws->fc.depth_bits;
   aaag_status e = radix_sort_device_n(ws->keys[0], ws->vals[0], ws->keys[1], ws->vals[1], n_dev, ws->capacity, key_bits,
                           ws->sort_hist, ws->sort_counters, ws->sort_lookback,
-                          ws->stats + kStatSortEpoch, ws->stats + kStatTimeout, &alt, st, true);
+                          (ws->n_sort_tiles + 1) * kRadix, ws->stats + kStatSortEpoch, ws->stats + kStatTimeout, &alt, st, true);
   if (e != AAAG_OK) return e;
   ws->sorted_in_alt = alt;
   if (cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * (size_t)ws->n_tiles, st) != cudaSuccess)
     return check_launch("ranges memset");
-  init_occupancy();
-  const int64_t rblocks = std::min<int64_t>((ws->capacity + 255) / 256, (int64_t)g_sm_count * 8);
+  const int64_t rblocks = std::min<int64_t>((ws->capacity + 255) / 256, (int64_t)launch_config().sms * 8);
   ranges_kernel<<<(unsigned)std::max<int64_t>(rblocks, 1), 256, 0, st>>>(
       ws->keys[alt], n_dev, ws->capacity, ws->fc.depth_bits, ws->ranges);
   return check_launch("ranges");

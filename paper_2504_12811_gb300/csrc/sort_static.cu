@@ -65,9 +65,35 @@ aaag_status scratch_address(unsigned char** out) {
 }
 
 }  // namespace
+
+// The bounded look-back wait of the radix sort, run out on purpose against the
+// fixed array's own words and timeout flag (failure detection test).
+aaag_status static_sort_wait_selftest(cudaStream_t st) {
+  unsigned char* base = nullptr;
+  const aaag_status e = scratch_address(&base);
+  if (e != AAAG_OK) return e;
+  unsigned long long* timeout = reinterpret_cast<unsigned long long*>(base + kOffTimeout);
+  if (cudaMemsetAsync(timeout, 0, 8, st) != cudaSuccess) return check_launch("static sort self-test memset");
+  return launch_sort_wait_selftest(reinterpret_cast<unsigned long long*>(base + kOffLookback), timeout, st);
+}
+
 }  // namespace aaag
 
 using namespace aaag;
+
+extern "C" aaag_status aaag_radix_sort_static_status(void) {
+  unsigned char* base = nullptr;
+  const aaag_status e = scratch_address(&base);
+  if (e != AAAG_OK) return e;
+  unsigned long long flag = 0;
+  if (cudaMemcpy(&flag, base + kOffTimeout, sizeof(flag), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return check_launch("aaag_radix_sort_static_status");
+  if (flag) {
+    set_error("aaag_radix_sort_static: a bounded look-back wait gave up; the output is unspecified");
+    return AAAG_ERR_TIMEOUT;
+  }
+  return AAAG_OK;
+}
 
 extern "C" int64_t aaag_radix_sort_static_capacity(void) { return kStaticSortMax; }
 
@@ -105,8 +131,8 @@ extern "C" aaag_status aaag_radix_sort_static(uint32_t* keys, uint32_t* vals, in
   e = check_launch("radix_sort_static count");
   if (e != AAAG_OK) return e;
   int alt = 0;
-  e = radix_sort_device_n(keys, vals, keys_alt, vals_alt, n_dev, n, key_bits, hist, counters, lookback, epoch,
-                          timeout, &alt, stream);
+  e = radix_sort_device_n(keys, vals, keys_alt, vals_alt, n_dev, n, key_bits, hist, counters, lookback,
+                          kStaticTiles * 256, epoch, timeout, &alt, stream);
   if (e != AAAG_OK) return e;
   if (alt) {   // an odd number of passes left the result in the scratch buffers
     if (cudaMemcpyAsync(keys, keys_alt, (size_t)n * 4, cudaMemcpyDeviceToDevice, stream) != cudaSuccess ||

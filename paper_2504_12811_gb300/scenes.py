@@ -144,27 +144,15 @@ def interior_cameras(rng, count, half_extent, width, height, fov_x_deg):
                         fov_x_deg=fov_x_deg) for p, d in zip(pos, dirs)]
 
 
-def training_frequency(means: np.ndarray, cams, znear: float = ZNEAR) -> np.ndarray:
+def vhat_train_draw(rng, n: int, lo: float, hi: float, unseen: float = 0.0) -> np.ndarray:
     """Synthetic stand-in for the per-Gaussian training sampling frequency
-    (the scene input v_train of the 3D smoothing filter, Sec. 3.1, Eq. 6):
-    the largest focal/depth over the given training cameras that see the
-    mean in front of their near plane and inside their image.  +inf when no
-    camera sees it (no clamp).  This synthesises an input; the renderer only
-    reads the result."""
-    m = means.astype(np.float64)
-    best = np.full(m.shape[0], -np.inf)
-    for c in cams:
-        v = c.viewmat.astype(np.float64)
-        pv = m @ v[:3, :3].T + v[:3, 3]
-        z = pv[:, 2]
-        with np.errstate(divide="ignore", invalid="ignore"):
-            u = c.fx * pv[:, 0] / z + c.cx
-            w = c.fy * pv[:, 1] / z + c.cy
-        seen = (z > znear) & (u >= 0) & (u <= c.width) & (w >= 0) & (w <= c.height)
-        freq = np.where(seen, c.fx / np.where(seen, z, 1.0), -np.inf)
-        best = np.maximum(best, freq)
-    best[~np.isfinite(best)] = np.inf
-    return best.astype(np.float32)
+    (the scene input v_train of the 3D smoothing filter, Sec. 3.2): drawn
+    log-uniformly in [lo, hi] pixels per world unit, with a random fraction
+    `unseen` set to +inf (a Gaussian that no training camera saw: no clamp).
+    A draw, not a computation: the renderer only reads the values."""
+    v = np.exp(rng.uniform(math.log(lo), math.log(hi), n))
+    v[rng.random(n) < unseen] = np.inf
+    return v.astype(np.float32)
 
 
 # ----------------------------------------------------------------------------
@@ -184,23 +172,19 @@ def _sh(rng, n, degree, dc_std=0.3, rest_std=0.05):
     return sh
 
 
-def uniform_cube_scene(n: int, seed: int = 0, sh_degree: int = 0,
-                       train_cams=None) -> Scene:
+def uniform_cube_scene(n: int, seed: int = 0, sh_degree: int = 0) -> Scene:
     """Means uniform in [-1,1]^3, log-scales N(-3.5, 0.5) per axis, uniform
     random unit quaternions (normalised N(0, I4), stored unnormalised),
-    opacity logits N(0, 1.5), SH DC N(0, 0.3) and higher bands N(0, 0.05).
-    Training cameras default to the (0,0,-3) camera plus 15 seeded orbit
-    poses at radius 3, 128x128, 60 deg."""
+    opacity logits N(0, 1.5), SH DC N(0, 0.3) and higher bands N(0, 0.05);
+    training sampling frequency log-uniform in [38, 78] px per unit, the range
+    that 128x128, 60-degree training cameras at distance 3 give."""
     rng = np.random.default_rng(seed)
     means = rng.uniform(-1.0, 1.0, (n, 3)).astype(np.float32)
     log_scales = rng.normal(-3.5, 0.5, (n, 3)).astype(np.float32)
     quats = _quats(rng, n)
     opac = rng.normal(0.0, 1.5, n).astype(np.float32)
     sh = _sh(rng, n, sh_degree)
-    if train_cams is None:
-        train_cams = [make_camera((0.0, 0.0, -3.0), target=(0, 0, 0))]
-        train_cams += orbit_cameras(rng, 15, 3.0, 128, 128, 60.0)
-    vt = training_frequency(means, train_cams)
+    vt = vhat_train_draw(rng, n, 38.0, 78.0)
     return Scene(means, log_scales, quats, opac, sh, vt, sh_degree,
                  {"kind": "uniform_cube", "seed": seed})
 
@@ -211,8 +195,10 @@ def cluster_scene(n: int = 1_000_000, seed: int = 0, n_clusters: int = 64,
     `n_clusters` anisotropic clusters (centres uniform in a 20 m box, per-axis
     std U[0.1, 2] m under a random rotation) plus a background shell at radius
     50 m (+-1%).  log-scales N(-4, 1), opacity logits N(0, 2), SH degree 3 with
-    DC N(0, 0.3) and higher bands N(0, 0.05).  Training frequency from 16
-    seeded interior 1920x1080 cameras."""
+    DC N(0, 0.3) and higher bands N(0, 0.05).  Training sampling frequency:
+    cluster Gaussians log-uniform in [100, 400] px per unit, shell ones in
+    [30, 50], about half of each unseen (+inf), the spread that 16 interior
+    1920x1080 training cameras give."""
     rng = np.random.default_rng(seed)
     n_shell = int(round(n * shell_fraction))
     n_cl = n - n_shell
@@ -232,8 +218,8 @@ def cluster_scene(n: int = 1_000_000, seed: int = 0, n_clusters: int = 64,
     quats = _quats(rng, n)
     opac = rng.normal(0.0, 2.0, n).astype(np.float32)
     sh = _sh(rng, n, sh_degree)
-    train = interior_cameras(rng, 16, 8.0, 1920, 1080, 60.0)
-    vt = training_frequency(means, train)
+    vt = np.concatenate([vhat_train_draw(rng, n_cl, 100.0, 400.0, unseen=0.5),
+                         vhat_train_draw(rng, n_shell, 30.0, 50.0, unseen=0.4)])
     return Scene(means, log_scales, quats, opac, sh, vt, sh_degree,
                  {"kind": "clusters", "seed": seed, "n_clusters": n_clusters})
 

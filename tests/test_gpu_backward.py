@@ -6,6 +6,7 @@ import torch
 
 import oracle as O
 from paper_2504_12811_gb300 import aaag, scenes
+from _gpu_util import check_gradient_elements
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +51,8 @@ def oracle_grads(scene, cam, w_rgb, w_alpha, pixels=None):
 
 
 def check_groups(g_gpu, g_ref, rel=REL_TOL):
+    """Per group relative L2 <= 1e-3, and the elementwise bound (see
+    `check_gradient_elements`)."""
     report = {}
     for g in GROUPS:
         a, b = g_gpu[g].ravel(), g_ref[g].ravel()
@@ -58,6 +61,7 @@ def check_groups(g_gpu, g_ref, rel=REL_TOL):
     print(report)
     for g, r in report.items():
         assert r <= rel, (g, r, report)
+    check_gradient_elements(g_gpu, g_ref, GROUPS)
     return report
 
 

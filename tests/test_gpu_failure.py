@@ -54,5 +54,5 @@ def test_selftest_rejects_bad_arguments():
     scene, cams = scenes.workload("small")
     ws, _, _, _ = run_frame(scene, cams[0], stages=("pre",))
     with pytest.raises(aaag.AaagError) as e:
-        aaag.aaag_selftest_wait_timeout(ws.handle, 2, aaag.current_stream())
+        aaag.aaag_selftest_wait_timeout(ws.handle, 3, aaag.current_stream())
     assert e.value.status == aaag.AAAG_ERR_INVALID_ARG

@@ -23,7 +23,7 @@ def scene1m():
     return scenes.workload("scene1m")
 
 
-@pytest.mark.parametrize("pose", [0, 5])
+@pytest.mark.parametrize("pose", [0, 5, 9, 13])
 def test_scene1m_sampled_pixels(scene1m, pose):
     scene, poses = scene1m
     cam = poses[pose]
@@ -33,19 +33,24 @@ def test_scene1m_sampled_pixels(scene1m, pose):
     st = aaag.stats(ws)
     torch.cuda.synchronize()
     rng = np.random.default_rng(11 + pose)
-    m = 480
+    m = 512
     px = rng.integers(0, cam.width, m)
     py = rng.integers(0, cam.height, m)
     prep = O.prepare(scene, cam)
     ref, ref_a = O.render_pixels(scene, cam, px, py, prep=prep)
-    amb = O.ambiguous_pixels(prep, px, py).numpy()
+    amb = np.concatenate([O.ambiguous_pixels(prep, px[i:i + 128], py[i:i + 128]).numpy()
+                          for i in range(0, m, 128)])
     g = rgb.cpu().numpy()[:, py, px].T.astype(np.float64)
     ga = alpha.cpu().numpy()[py, px].astype(np.float64)
     err = np.maximum(np.abs(g - ref.numpy()).max(1), np.abs(ga - ref_a.numpy()))
     print(f"pose {pose}: stats={st} max|err| clean={err[~amb].max():.3e} all={err.max():.3e} "
           f"ambiguous={amb.mean():.4f} psnr={psnr(g, ref.numpy()):.1f}")
-    assert amb.mean() < TOL_AMBIG * 5
-    assert err[~amb].max() <= TOL_ABS
+    assert st["misorders"] == 0
+    if err.max() > TOL_ABS:
+        # only a rare pixel whose decisions sit within float32 reach of a
+        # threshold may be excused
+        assert amb.mean() < TOL_AMBIG
+        assert err[~amb].max() <= TOL_ABS
     assert psnr(g, ref.numpy()) >= TOL_PSNR
 
 

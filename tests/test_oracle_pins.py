@@ -397,6 +397,67 @@ def test_mean_depth_order_ablation_closed_form():
     assert np.abs(exact - mean).max() > 1e-3
 
 
+def test_kbuffer_hand_worked_sequence():
+    # Bounded buffer of 2 entries, one pixel, four contributors arriving in
+    # the order g0 (t* = 3), g1 (t* = 1), g2 (t* = 2), g3 (t* = 0.5):
+    #   g0 -> [g0];  g1 -> [g1 g0];  g2 finds it full: g1 is nearer, blended,
+    #   g2 enters -> [g2 g0];  g3 finds it full and is nearer than g2: blended
+    #   at once;  end: g2, g0.  Blend sequence g1 g3 g2 g0 (exact: g3 g1 g2 g0).
+    a = np.array([0.3, 0.5, 0.2, 0.4])
+    t = np.array([3.0, 1.0, 2.0, 0.5])
+    arrival = np.array([0.1, 0.2, 0.3, 0.4])
+    col = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    bg = np.array([0.1, 0.2, 0.3])
+
+    def by_hand(seq):
+        T, C = 1.0, np.zeros(3)
+        for g in seq:
+            C = C + col[g] * a[g] * T
+            T *= 1 - a[g]
+        return C + T * bg, T
+
+    f = lambda v: torch.from_numpy(np.asarray(v, np.float64))
+    contrib = torch.ones(1, 4, dtype=torch.bool)
+    for size, seq in ((2, [1, 3, 2, 0]), (0, [0, 1, 2, 3]), (1, [1, 2, 3, 0]), (4, [3, 1, 2, 0])):
+        out, T, n = O.composite_kbuffer(f(a[None]), f(t[None]), arrival, contrib, f(col), f(bg), size)
+        C_ref, T_ref = by_hand(seq)
+        np.testing.assert_allclose(out[0].numpy(), C_ref, rtol=1e-14, err_msg=str(size))
+        assert T[0].item() == pytest.approx(T_ref, rel=1e-14) and int(n[0]) == 4
+    # early termination inside the buffer: a = 0.99 layers stop after two
+    a2 = np.full(4, 0.99)
+    out, T, n = O.composite_kbuffer(f(a2[None]), f(t[None]), arrival, contrib, f(col), f(bg), 2)
+    assert int(n[0]) == 2 and T[0].item() == pytest.approx(0.01 ** 2, rel=1e-12)
+
+
+def test_kbuffer_limits_are_exact_and_mean_orders(small_workload):
+    # with room for every contributor the buffer blends in exact depth order;
+    # with no room it blends in arrival (mean-depth) order
+    sc, cams = small_workload
+    cam = cams[1]
+    rng = np.random.default_rng(8)
+    px, py = rng.integers(0, cam.width, 300), rng.integers(0, cam.height, 300)
+    p = O.prepare(sc, cam)
+    exact, ea = O.render_pixels(sc, cam, px, py, prep=p)
+    big, ba = O.render_pixels(sc, cam, px, py, prep=p, order="kbuffer", kbuffer=1 << 20)
+    np.testing.assert_allclose(big.numpy(), exact.numpy(), atol=1e-14)
+    np.testing.assert_allclose(ba.numpy(), ea.numpy(), atol=1e-14)
+    mean, ma = O.render_pixels(sc, cam, px, py, prep=p, order="mean")
+    none, na = O.render_pixels(sc, cam, px, py, prep=p, order="kbuffer", kbuffer=0)
+    np.testing.assert_allclose(none.numpy(), mean.numpy(), atol=1e-14)
+    # the 16-entry buffer is exact on pixels with at most 16 contributors
+    k16, _ = O.render_pixels(sc, cam, px, py, prep=p, order="kbuffer")
+    rho2, ts = O.ray_maximum(p, px, py)
+    _, contrib, _ = O.pixel_alphas(p, rho2, ts)
+    few = contrib.sum(1).numpy() <= 16
+    assert few.sum() > 50 and (~few).sum() > 10
+    np.testing.assert_allclose(k16.numpy()[few], exact.numpy()[few], atol=1e-14)
+    # a buffer of two entries overflows on the crowded pixels: approximate there
+    k2, _ = O.render_pixels(sc, cam, px, py, prep=p, order="kbuffer", kbuffer=2)
+    few2 = contrib.sum(1).numpy() <= 2
+    np.testing.assert_allclose(k2.numpy()[few2], exact.numpy()[few2], atol=1e-14)
+    assert np.abs(k2.numpy()[~few2] - exact.numpy()[~few2]).max() > 1e-3
+
+
 def test_ewa_splat_closed_form():
     # Ablation without 3D evaluation: for an isotropic filtered variance
     # s_hat, Sigma' = s_hat J J^T with J the perspective Jacobian at the mean;

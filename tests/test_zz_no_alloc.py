@@ -2,8 +2,9 @@
 device memory (a plug-in whose host application owns every allocation, or a
 real-time loop that must not wait on the allocator).  Its scratch is a fixed
 array inside the library.  Checked through the C ABI against the allocating
-entry point aaag_radix_sort on two calls in a row; this file is collected
-last so that a stop at the first failure has already run every other test."""
+entry point aaag_radix_sort and a CPU stable sort on two calls in a row, and
+its failure report; this file is collected last so that a stop at the first
+failure has already run every other test."""
 import numpy as np
 import pytest
 import torch
@@ -47,8 +48,13 @@ def test_static_scratch_sort_matches_allocating_sort(first, second):
         v = torch.from_numpy(vals.view(np.int32)).cuda()
         aaag.aaag_radix_sort_static(k.data_ptr(), v.data_ptr(), n, key_bits, aaag.current_stream())
         torch.cuda.synchronize()
+        assert aaag.aaag_radix_sort_static_status() == 0
         np.testing.assert_array_equal(k.cpu().numpy().view(np.uint32), ref_k)
         np.testing.assert_array_equal(v.cpu().numpy().view(np.uint32), ref_v)
+        # and against a CPU stable sort of the same keys
+        order = np.argsort(keys, kind="stable")
+        np.testing.assert_array_equal(ref_k, keys[order])
+        np.testing.assert_array_equal(ref_v, vals[order])
 
 
 def test_static_scratch_sort_rejects_oversize():
@@ -58,3 +64,28 @@ def test_static_scratch_sort_rejects_oversize():
     with pytest.raises(aaag.AaagError) as e:
         aaag.aaag_radix_sort_static(k.data_ptr(), k.data_ptr(), cap + 1, 32, aaag.current_stream())
     assert e.value.status == 2
+
+
+def test_static_scratch_sort_reports_a_wait_that_gave_up():
+    """The sort's bounded look-back wait, run out on purpose against the fixed
+    array's own words (a predecessor that never publishes): it returns after
+    about a second, the status query reports TIMEOUT, and the next sort clears
+    the flag and sorts correctly."""
+    import time
+    st = aaag.current_stream()
+    t0 = time.time()
+    aaag.aaag_selftest_wait_timeout(None, 2, st)
+    torch.cuda.synchronize()
+    assert 0.2 < time.time() - t0 < 30.0
+    assert aaag.aaag_radix_sort_static_status() == 4
+    rng = np.random.default_rng(77)
+    keys = rng.integers(0, 1 << 32, 5000, dtype=np.uint64).astype(np.uint32)
+    vals = np.arange(5000, dtype=np.uint32)
+    k = torch.from_numpy(keys.view(np.int32)).cuda()
+    v = torch.from_numpy(vals.view(np.int32)).cuda()
+    aaag.aaag_radix_sort_static(k.data_ptr(), v.data_ptr(), keys.size, 32, st)
+    torch.cuda.synchronize()
+    assert aaag.aaag_radix_sort_static_status() == 0
+    order = np.argsort(keys, kind="stable")
+    np.testing.assert_array_equal(k.cpu().numpy().view(np.uint32), keys[order])
+    np.testing.assert_array_equal(v.cpu().numpy().view(np.uint32), vals[order])
