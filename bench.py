@@ -39,8 +39,8 @@ WORKLOAD = "scene1m: 1,000,000 Gaussians (64 clusters + 10% shell, SH 3), 1920x1
 OPS_PER_EVAL = 40
 # Mean DRAM bytes (read + write) of one render launch over the 16 poses of the
 # workload, from an ncu capture of the current kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum, cold cache); None until one is taken.
-RENDER_DRAM_BYTES = None
+# dram__bytes_write.sum, cold cache; profiles/render_kernel_scene1m_1080p.md).
+RENDER_DRAM_BYTES = 16.02e6
 FP32_LANES_PER_SM = 128
 
 
@@ -55,8 +55,11 @@ def parse():
     ap.add_argument("--no-hbm-large", action="store_true", help="skip preprocess and sort at 16M / 64M")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--capacity", type=int, default=48 << 20)
-    ap.add_argument("--serve", default="400:2,60:10",
+    ap.add_argument("--serve", default="400:3,30:10",
                     help="serving traces as rate_hz:seconds pairs ('' = skip serving)")
+    ap.add_argument("--serve-warmup", type=float, default=0.0,
+                    help="seconds at the start of each trace whose requests run but are not counted")
+    ap.add_argument("--serve-policies", default="all", help="'all' or 'server,plain'")
     ap.add_argument("--serve-capacity", type=int, default=1 << 28)
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     ap.add_argument("--sort-keys", type=int, default=0,
@@ -120,7 +123,9 @@ def run_serving(args, dev):
     out = {"scenes": {k: v.n for k, v in sc.items()},
            "mix": "equal thirds: 640x480 60deg, 1920x1080 60deg, stereo 2x1832x1920 110deg; "
                   "poses uniform in [-0.8,0.8]^3 inside the scene, uniform look directions",
-           "latency": "host-observed completion (image in device memory) minus arrival",
+           "latency": "host-observed completion (images of every view copied to pinned host memory) "
+                      "minus arrival",
+           "warmup_s": args.serve_warmup,
            "generation_s": gen_s, "runs": []}
     for spec in [x for x in args.serve.split(",") if x]:
         rate, seconds = (float(v) for v in spec.split(":"))
@@ -129,20 +134,23 @@ def run_serving(args, dev):
         server = serve.Server(sc, int(args.serve_budget_gb * 2**30), 1920, 1920, args.serve_capacity,
                               max_batch_views=8, device=dev)
         n_slots = len(server.slots)
+        all_policies = args.serve_policies == "all"
+        lat_u = lat_f = lat_b = None
         try:
             server.warm(trace)
             t = time.time()
             lat = server.serve_streams(trace, urgent_pixels=1920 * 1080, heavy_pixels=1920 * 1080)
             ours_wall = time.time() - t
-            t = time.time()
-            lat_u = server.serve_streams(trace, urgent_pixels=640 * 480)
-            urgent_wall = time.time() - t
-            t = time.time()
-            lat_f = server.serve_streams(trace)
-            fifo_wall = time.time() - t
-            t = time.time()
-            lat_b = server.serve(trace)
-            batch_wall = time.time() - t
+            if all_policies:
+                t = time.time()
+                lat_u = server.serve_streams(trace, urgent_pixels=640 * 480)
+                urgent_wall = time.time() - t
+                t = time.time()
+                lat_f = server.serve_streams(trace)
+                fifo_wall = time.time() - t
+                t = time.time()
+                lat_b = server.serve(trace)
+                batch_wall = time.time() - t
         finally:
             server.close()
         del server
@@ -151,21 +159,30 @@ def run_serving(args, dev):
         lat_p = serve.plain_renderer(sc, trace, 1920, 1920, args.serve_capacity, device=dev)
         plain_wall = time.time() - t
         torch.cuda.empty_cache()
-        out["runs"].append({
-            "rate_hz": rate, "seconds": seconds, "requests": len(trace), "views": n_views,
-            "server": dict(serve.latency_summary(lat, max(ours_wall, seconds), n_views), slots=n_slots,
-                           budget_gb=args.serve_budget_gb, wall_s=ours_wall,
-                           mode="per-request pipelines; stereo requests one at a time in arrival order, "
-                                "the others overtake them on high-priority streams"),
-            "server_priority_only": dict(serve.latency_summary(lat_u, max(urgent_wall, seconds), n_views),
-                                         wall_s=urgent_wall,
-                                         mode="per-request pipelines, 640x480 requests on high-priority streams"),
-            "server_no_priority": dict(serve.latency_summary(lat_f, max(fifo_wall, seconds), n_views),
-                                       wall_s=fifo_wall, mode="per-request pipelines"),
-            "server_batches": dict(serve.latency_summary(lat_b, max(batch_wall, seconds), n_views),
-                                   wall_s=batch_wall, mode="batch barrier, 8 views, 2 in flight"),
-            "plain_per_frame": dict(serve.latency_summary(lat_p, max(plain_wall, seconds), n_views),
-                                    wall_s=plain_wall)})
+        # requests of the warm-up seconds run but are not counted
+        keep = [k for k, r in enumerate(trace) if r.arrival >= args.serve_warmup]
+        kept_views = sum(len(trace[k].cams) for k in keep)
+        span = max(seconds - args.serve_warmup, 1e-9)
+
+        def summary(lat_s, wall):
+            # rate over the counted requests: their number over the time from the
+            # first counted arrival to the last counted completion
+            done = max(trace[k].arrival + lat_s[k] for k in keep)
+            busy = max(done - args.serve_warmup, span)
+            return serve.latency_summary([lat_s[k] for k in keep], busy, kept_views)
+        run = {"rate_hz": rate, "seconds": seconds, "warmup_s": args.serve_warmup, "requests": len(keep),
+               "views": kept_views,
+               "server": dict(summary(lat, ours_wall), slots=n_slots, budget_gb=args.serve_budget_gb, wall_s=ours_wall,
+                              mode="per-request pipelines; stereo requests one at a time in arrival order, "
+                                   "the others overtake them on high-priority streams"),
+               "plain_per_frame": dict(summary(lat_p, plain_wall), wall_s=plain_wall)}
+        if all_policies:
+            run["server_priority_only"] = dict(summary(lat_u, urgent_wall), wall_s=urgent_wall,
+                                               mode="per-request pipelines, 640x480 requests on high-priority streams")
+            run["server_no_priority"] = dict(summary(lat_f, fifo_wall), wall_s=fifo_wall, mode="per-request pipelines")
+            run["server_batches"] = dict(summary(lat_b, batch_wall), wall_s=batch_wall,
+                                         mode="batch barrier, 8 views, 2 in flight")
+        out["runs"].append(run)
     return out
 
 
@@ -750,8 +767,8 @@ def run_ours(args):
     e2e_value = job_rate(e2e_steps, e0.elapsed_time(e1))
 
     # set_frame + preprocess test + preprocess; cull: offsets + test + emit;
-    # sort: histogram + radix passes + ranges; render
-    launches_per_frame = 3 + 3 + (2 + passes) + 1
+    # sort: histogram + radix passes + ranges; render: tile order + render
+    launches_per_frame = 3 + 3 + (2 + passes) + 2
     mean = lambda key: float(np.mean([p[key] for p in per_pose]))
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,

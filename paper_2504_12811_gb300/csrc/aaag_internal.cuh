@@ -95,8 +95,10 @@ enum StatSlot : int {
   kStatBatchCounter = 16,  // uint32 work-item counter of the batched render
   kStatSortEpoch = 17,
   kStatFrameEpoch = 18,    // bumped by every frame's constants: tags the cull look-back words
-  kStatCount = 19
+  kStatRenderCounter = 19, // uint32 tile counter of the persistent render
+  kStatCount = 20
 };
+
 
 }  // namespace aaag
 
@@ -127,6 +129,7 @@ struct aaag_workspace {
   uint32_t* sort_counters;       // [4] tile counters per pass
   unsigned long long* sort_lookback;   // [max sort tiles][256]
   uint2* ranges;                 // [n_tiles]
+  uint32_t* tile_order;          // [n_tiles] render order (longest tiles first)
   float* final_T;                // [H*W]
   uint32_t* n_blended;           // [H*W]
   unsigned long long* stats;     // [kStatCount]

@@ -60,7 +60,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
   size_t records, aux, cand, counts, offsets, owner, mask, cull_lb, keys0, keys1, vals0, vals1, hist, counters,
-      lookback, ranges, final_T, n_blended, stats, grad, fc, total;
+      lookback, ranges, order, final_T, n_blended, stats, grad, fc, total;
 };
 
 int tiles_of(int size) { return (size + kTile - 1) / kTile; }
@@ -96,6 +96,7 @@ Layout layout_of(int64_t n, int w, int h, int64_t cap) {
   L.counters = take(4 * 4);
   L.lookback = take((size_t)nst * 256 * 8);
   L.ranges = take(ntiles * sizeof(uint2));
+  L.order = take(ntiles * sizeof(uint32_t));
   L.final_T = take((size_t)w * h * 4);
   L.n_blended = take((size_t)w * h * 4);
   L.stats = take(kStatCount * 8);
@@ -317,6 +318,7 @@ aaag_status aaag_workspace_init(void* dev_mem, size_t bytes, int64_t n, int32_t 
   w->sort_counters = reinterpret_cast<uint32_t*>(b + L.counters);
   w->sort_lookback = reinterpret_cast<unsigned long long*>(b + L.lookback);
   w->ranges = reinterpret_cast<uint2*>(b + L.ranges);
+  w->tile_order = reinterpret_cast<uint32_t*>(b + L.order);
   w->final_T = reinterpret_cast<float*>(b + L.final_T);
   w->n_blended = reinterpret_cast<uint32_t*>(b + L.n_blended);
   w->stats = reinterpret_cast<unsigned long long*>(b + L.stats);

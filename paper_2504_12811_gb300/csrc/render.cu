@@ -106,15 +106,63 @@ __device__ __forceinline__ void render_tile(TileSmem<IndexQueue>& s, int tile, c
   }
 }
 
+// Tile order of the persistent render: tiles in descending order of their
+// pair counts (two buckets per octave), so that the longest tiles start first
+// and the short ones fill in behind them.  One block; also resets the work
+// counter.
+__global__ void __launch_bounds__(1024)
+tile_order_kernel(const uint2* __restrict__ ranges, const FrameConst* __restrict__ fcp,
+                  uint32_t* __restrict__ order, uint32_t* __restrict__ counter) {
+  __shared__ uint32_t base[64];
+  const int n_tiles = fcp->tiles_x * fcp->tiles_y;
+  auto bucket = [&](int t) {
+    const uint2 r = ranges[t];
+    const uint32_t c = r.y - r.x + 1u;
+    const int lz = 32 - __clz(c);                                   // 1..32
+    const int half = lz >= 2 ? (int)((c >> (lz - 2)) & 1u) : 0;
+    return 63 - min(63, 2 * lz + half);                            // longest first
+  };
+  if (threadIdx.x < 64) base[threadIdx.x] = 0;
+  if (threadIdx.x == 0) *counter = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&base[bucket(t)], 1u);
+  __syncthreads();
+  if (threadIdx.x < 32) {   // exclusive scan of 64 counts, two per lane
+    const uint32_t c0 = base[2 * threadIdx.x], c1 = base[2 * threadIdx.x + 1];
+    uint32_t incl = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)threadIdx.x >= o) incl += v;
+    }
+    const uint32_t excl = incl - c0 - c1;
+    base[2 * threadIdx.x] = excl;
+    base[2 * threadIdx.x + 1] = excl + c0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&base[bucket(t)], 1u)] = (uint32_t)t;
+}
+
+// Persistent: blocks take tiles in the order above from a work counter.
 __global__ void __launch_bounds__(kTilePixels, 3)
 render_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
               const uint32_t* __restrict__ vals, const Record* __restrict__ rec, const uint4* __restrict__ aux,
               const FrameConst* __restrict__ fcp, float* __restrict__ rgb, float* __restrict__ alpha,
-              float* __restrict__ final_T, uint32_t* __restrict__ n_blended, unsigned long long* __restrict__ stats) {
+              float* __restrict__ final_T, uint32_t* __restrict__ n_blended, unsigned long long* __restrict__ stats,
+              const uint32_t* __restrict__ order, uint32_t* __restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileSmem<IndexQueue>& s = *reinterpret_cast<TileSmem<IndexQueue>*>(smem_raw);
+  __shared__ uint32_t s_item;
   const FrameConst fc = *fcp;
-  render_tile(s, blockIdx.x, ranges, keys, vals, rec, aux, fc, rgb, alpha, final_T, n_blended, stats);
+  const uint32_t n_tiles = (uint32_t)(fc.tiles_x * fc.tiles_y);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    __syncthreads();
+    if (item >= n_tiles) break;
+    render_tile(s, (int)order[item], ranges, keys, vals, rec, aux, fc, rgb, alpha, final_T, n_blended, stats);
+  }
 }
 
 // ---- K8: one persistent launch over the tiles of several frames.
@@ -208,11 +256,16 @@ aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, fl
 }
 
 aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st) {
-  launch_config();   // function attributes of this device
+  const LaunchConfig& lc = launch_config();
   const int alt = ws->sorted_in_alt;
-  render_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kForwardSmemBytes, st>>>(ws->ranges, ws->keys[alt], ws->vals[alt],
-                                                               ws->records, ws->aux, ws->fc_dev, rgb, alpha, ws->final_T,
-                                                               ws->n_blended, ws->stats);
+  uint32_t* counter = reinterpret_cast<uint32_t*>(ws->stats + kStatRenderCounter);
+  tile_order_kernel<<<1, 1024, 0, st>>>(ws->ranges, ws->fc_dev, ws->tile_order, counter);
+  aaag_status e = check_launch("tile_order");
+  if (e != AAAG_OK) return e;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)lc.sms * lc.serve_per_sm, ws->n_tiles));
+  render_kernel<<<grid, kTilePixels, kForwardSmemBytes, st>>>(ws->ranges, ws->keys[alt], ws->vals[alt], ws->records,
+                                                               ws->aux, ws->fc_dev, rgb, alpha, ws->final_T,
+                                                               ws->n_blended, ws->stats, ws->tile_order, counter);
   return check_launch("render");
 }
 

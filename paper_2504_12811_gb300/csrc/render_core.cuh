@@ -59,6 +59,8 @@
 // the bounds), so the blends and their order are unchanged.
 #pragma once
 
+#include <type_traits>
+
 #include "aaag_internal.cuh"
 
 namespace aaag {
@@ -68,7 +70,8 @@ constexpr int kQueue = 16;   // per-pixel re-sort queue entries (power of two)
 // Coefficients of the staged Gaussians (one batch of pairs of one tile).
 struct StageSmem {
   float4 a[kTilePixels];    // N0.xyz, o_hat
-  float4 b[kTilePixels];    // Nx.xyz, mask of the warps holding a pixel that can see it (bits)
+  float4 b[kTilePixels];    // Nx.xyz, ub | wmask: an upper bound of t* over the tile whose
+                            // low 8 bits are the mask of the warps holding a pixel that can see it
   float4 c[kTilePixels];    // Ny.xyz, tau+: |num|^2 > tau+ |d|^2 rules out alpha >= 1/255
   float4 d[kTilePixels];    // D0.xyz, G.x
   float4 e[kTilePixels];    // Dx.xyz, G.y
@@ -139,6 +142,46 @@ __device__ __forceinline__ float3 crs(float3 a, float3 b) {
   return f3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
 }
 
+// An upper bound of the depth t* = G.d / |d|^2 of the ray maximum over the
+// tile's pixel centres (d = D0 + x Dx + y Dy, x and y in [0.5, 15.5]): the
+// largest G.d (affine: at a corner) over the smallest |d|^2 on the rectangle
+// (convex: its unconstrained minimum when that lies inside, else the minimum
+// along one of the edges), raised by 0.1% against rounding.  Returned as float
+// bits rounded up to a multiple of 256 (the low 8 bits then carry the warp
+// mask and only raise it); a huge finite value when there is no bound.  A
+// later depth-peeling pass skips the Gaussian when this is below its window.
+__device__ __forceinline__ uint32_t tile_depth_cap(float3 D0, float3 Dx, float3 Dy, float3 G) {
+  const uint32_t kNone = 0x7f000000u;   // about 1.7e38
+  const float g0 = dot3(G, D0), gx = dot3(G, Dx), gy = dot3(G, Dy);
+  const float gmax = g0 + fmaxf(0.5f * gx, 15.5f * gx) + fmaxf(0.5f * gy, 15.5f * gy);
+  if (!(gmax > 0.0f)) return kNone;
+  const float a = dot3(Dx, Dx), b = dot3(Dx, Dy), c = dot3(Dy, Dy);
+  const float e = dot3(D0, Dx), f = dot3(D0, Dy);
+  auto q = [&](float x, float y) {
+    const float3 d = fma3(y, Dy, fma3(x, Dx, D0));
+    return dot3(d, d);
+  };
+  auto clampc = [](float v) { return fminf(fmaxf(v, 0.5f), 15.5f); };
+  float qmin = 3.0e38f;
+  const float det = a * c - b * b;
+  if (det > 0.0f) {
+    const float x = (b * f - c * e) / det, y = (b * e - a * f) / det;
+    if (x >= 0.5f && x <= 15.5f && y >= 0.5f && y <= 15.5f) qmin = q(x, y);
+  }
+  if (c > 0.0f) {
+    qmin = fminf(qmin, q(0.5f, clampc(-(f + 0.5f * b) / c)));
+    qmin = fminf(qmin, q(15.5f, clampc(-(f + 15.5f * b) / c)));
+  }
+  if (a > 0.0f) {
+    qmin = fminf(qmin, q(clampc(-(e + 0.5f * b) / a), 0.5f));
+    qmin = fminf(qmin, q(clampc(-(e + 15.5f * b) / a), 15.5f));
+  }
+  qmin = fminf(qmin, fminf(fminf(q(0.5f, 0.5f), q(15.5f, 0.5f)), fminf(q(0.5f, 15.5f), q(15.5f, 15.5f))));
+  const float ub = gmax / qmin * 1.001f;
+  if (!(qmin > 0.0f) || !(ub < 1.0e37f)) return kNone;
+  return (__float_as_uint(ub) + 0x100u) & ~0xffu;
+}
+
 // Coefficients of one Gaussian for the tile at (ox, oy) (cxm = cx - ox,
 // cym = cy - oy); rect: its pixel-centre ranges.
 __device__ __forceinline__ void stage_one(StageSmem& s, int slot, const Record* rec, uint32_t gid, uint2 rect,
@@ -161,7 +204,7 @@ __device__ __forceinline__ void stage_one(StageSmem& s, int slot, const Record* 
   const float fxfy = fc.fx * fc.fy;
   const float3 G = fxfy * fma3(t1.w, crs(A2, T3), fma3(t2.w, crs(T3, A1), t3.w * crs(A1, A2)));
   s.a[slot] = make_float4(N0.x, N0.y, N0.z, cw.w);
-  s.b[slot] = make_float4(Nx.x, Nx.y, Nx.z, __uint_as_float(warp_mask(rect, ox, oy)));
+  s.b[slot] = make_float4(Nx.x, Nx.y, Nx.z, __uint_as_float(tile_depth_cap(D0, Dx, Dy, G) | warp_mask(rect, ox, oy)));
   s.L[slot] = Lnext;
   // rho^2 <= tau_rho exactly where o_hat exp(-rho^2/2) >= 1/255; the margin
   // keeps the division-free prefilter conservative under float32 rounding
@@ -177,6 +220,7 @@ __device__ __forceinline__ void stage_one(StageSmem& s, int slot, const Record* 
 template <class Q>
 struct SmemQueue {
   static_assert(kQueue == 16, "the order word holds 16 four-bit slot numbers");
+  using P = typename Q::Payload;
   Q* q;
   int tid, n;
   unsigned long long order;   // nibble i: slot of the i-th nearest entry
@@ -184,7 +228,7 @@ struct SmemQueue {
   float ft;                   // t* of the nearest entry (n > 0)
   __device__ __forceinline__ int slot_at(int i) const { return (int)((order >> (4 * i)) & 15ull); }
   // remove the nearest entry, returning its alpha and payload
-  __device__ __forceinline__ void pop(float& a, typename Q::Payload& p) {
+  __device__ __forceinline__ void pop(float& a, P& p) {
     const int s = (int)(order & 15ull);
     q->load(s, tid, a, p);
     order >>= 4;
@@ -195,7 +239,7 @@ struct SmemQueue {
   template <class Blender>
   __device__ __forceinline__ void release(Blender& bl) {
     float a;
-    typename Q::Payload p;
+    P p;
     pop(a, p);
     bl.blend(a, p);
   }
@@ -212,7 +256,7 @@ struct SmemQueue {
     }
   }
   // sorted insert (n < kQueue), after every entry with an equal t*
-  __device__ __forceinline__ void insert(float t, float a, typename Q::Payload p) {
+  __device__ __forceinline__ void insert(float t, float a, P p) {
     int i = n;
     while (i > 0 && q->t(slot_at(i - 1), tid) > t) --i;
     const int s = __ffs(~used) - 1;   // a free slot: fewer than 16 are used
@@ -329,7 +373,7 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
             bool contrib = false;
             float ts = 0.0f, ca = 0.0f, Lnext = 0.0f;
             EvalState ev{k, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            if (open && !bl.done && jk >= jfirst) {
+            if (open && !bl.done && jk >= jfirst && !(bq.w < lo)) {
               ++neval;
               const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
               const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
@@ -402,75 +446,92 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
         }
         bl.end_batch(b0, cnt);
       } else if (open && !bl.done) {
-        // pairs before jfirst hold nothing for this pass of this pixel
-        const int k0 = jfirst > b0 ? (int)min((uint32_t)cnt, jfirst - b0) : 0;
-        for (int k = k0; k < cnt; ++k) {
-          const float4 bq = s.b[k];
-          if (!(__float_as_uint(bq.w) & wbit)) continue;   // warp-uniform
-          ++neval;
-          const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
-          const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
-          const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
-          const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
-          const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
-          const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
-          const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
-          const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
-          const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
-          // rho^2 > tau+ rules out alpha >= 1/255 without a division
-          if (nn <= c.w * dd) {
-            const float inv = __fdividef(1.0f, dd);
-            const float rho2 = nn * inv;
-            const float raw = a.w * __expf(-0.5f * rho2);
-            const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
-            if (raw >= kAlphaMin && ts >= fc.znear && ts >= lo && ts < hi) {
-              const float Lnext = by_key ? s.L[k] : -kInf;
-              const float ca = fminf(raw, kAlphaMax);
-              const EvalState ev{k, n0, n1, n2, d0, d1, d2, inv, rho2};
-              // 1. queued entries in front of the new one that nothing later can precede
-              while (q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext) q.release(bl);
-              if (!bl.done) {
-                if (ts < Lnext || !resort) {
-                  // 2. the new contributor, then the rest below L_next
-                  bl.blend_new(ca, ev);
-                  while (q.n > 0 && !bl.done && q.ft < Lnext) q.release(bl);
-                } else {
-                  // 3. queue it.  A full queue defers the farther of the new
-                  // entry and its last one to a later pass; in the
-                  // bounded-buffer ablation, or when its nearest entry lies at
-                  // lo, it releases the nearer of its front and the new entry
-                  bool insert = true;
-                  if (q.n == kQueue) {
-                    if (peel && q.ft > lo) {
-                      if (jnext == kNone) jnext = jfill;
-                      hi = fmaxf(ts, q.back_t());
-                      q.drop_from(hi);
-                      insert = ts < hi;
-                    } else {
-                      if (!peel) ++nmis;
-                      if (ts < q.ft) {
-                        bl.blend_new(ca, ev);
-                        insert = false;
+        // The first pass takes every pair from the tile's start with no lower
+        // window bound; a later one skips the pairs before jfirst (they hold
+        // nothing for this pixel's window) and tests lo.
+        auto pairs = [&](auto first) {
+          constexpr bool FIRST = decltype(first)::value;
+          int k0 = 0;
+          if constexpr (!FIRST) k0 = jfirst > b0 ? (int)min((uint32_t)cnt, jfirst - b0) : 0;
+          for (int k = k0; k < cnt; ++k) {
+            const float4 bq = s.b[k];
+            if (!(__float_as_uint(bq.w) & wbit)) continue;   // warp-uniform
+            if constexpr (!FIRST) {
+              if (bq.w < lo) continue;   // its t* lies in front of this pass's window
+            }
+            ++neval;
+            const float4 a = s.a[k], c = s.c[k], d = s.d[k], e = s.e[k], f = s.f[k];
+            const float n0 = fmaf(y, c.x, fmaf(x, bq.x, a.x));
+            const float n1 = fmaf(y, c.y, fmaf(x, bq.y, a.y));
+            const float n2 = fmaf(y, c.z, fmaf(x, bq.z, a.z));
+            const float d0 = fmaf(y, f.x, fmaf(x, e.x, d.x));
+            const float d1 = fmaf(y, f.y, fmaf(x, e.y, d.y));
+            const float d2 = fmaf(y, f.z, fmaf(x, e.z, d.z));
+            const float nn = fmaf(n2, n2, fmaf(n1, n1, n0 * n0));
+            const float dd = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+            // rho^2 > tau+ rules out alpha >= 1/255 without a division
+            if (nn <= c.w * dd) {
+              const float inv = __fdividef(1.0f, dd);
+              const float rho2 = nn * inv;
+              const float raw = a.w * __expf(-0.5f * rho2);
+              const float ts = fmaf(f.w, d2, fmaf(e.w, d1, d.w * d0)) * inv;
+              if (raw >= kAlphaMin && ts >= fc.znear && (FIRST || ts >= lo) && ts < hi) {
+                const float Lnext = by_key ? s.L[k] : -kInf;
+                const float ca = fminf(raw, kAlphaMax);
+                const EvalState ev{k, n0, n1, n2, d0, d1, d2, inv, rho2};
+                // 1. queued entries in front of the new one that nothing later can precede
+                while (q.n > 0 && !bl.done && q.ft <= ts && q.ft < Lnext) q.release(bl);
+                if (!bl.done) {
+                  if (ts < Lnext || !resort) {
+                    // 2. the new contributor, then the rest below L_next
+                    bl.blend_new(ca, ev);
+                    while (q.n > 0 && !bl.done && q.ft < Lnext) q.release(bl);
+                  } else {
+                    // 3. queue it.  A full queue defers the farther of the new
+                    // entry and its last one to a later pass; in the
+                    // bounded-buffer ablation, or when its nearest entry lies
+                    // at lo, it releases the nearer of its front and the new
+                    // entry instead
+                    bool insert = true;
+                    if (q.n == kQueue) {
+                      if (peel && q.ft > lo) {
+                        if (jnext == kNone) jnext = jfill;
+                        hi = fmaxf(ts, q.back_t());
+                        q.drop_from(hi);
+                        insert = ts < hi;
                       } else {
-                        q.release(bl);
+                        if (!peel) ++nmis;
+                        if (ts < q.ft) {
+                          bl.blend_new(ca, ev);
+                          insert = false;
+                        } else {
+                          q.release(bl);
+                        }
                       }
                     }
+                    if (insert && !bl.done) {
+                      if (q.n == 0) jfill = b0 + (uint32_t)k;
+                      q.insert(ts, ca, bl.payload(k));
+                    }
                   }
-                  if (insert && !bl.done) {
-                    if (q.n == 0) jfill = b0 + (uint32_t)k;
-                    q.insert(ts, ca, bl.payload(k));
+                  if constexpr (!FIRST) {
+                    // close the pass once no later pair can hold a contributor below hi
+                    if (Lnext >= hi) {
+                      while (q.n > 0 && !bl.done) q.release(bl);
+                      open = false;
+                      break;
+                    }
                   }
-                }
-                // close the pass once no later pair can hold a contributor below hi
-                if (Lnext >= hi) {
-                  while (q.n > 0 && !bl.done) q.release(bl);
-                  open = false;
-                  break;
                 }
               }
             }
+            if (bl.done) break;
           }
-          if (bl.done) break;
+        };
+        if (lo == -kInf) {
+          pairs(std::true_type{});
+        } else {
+          pairs(std::false_type{});
         }
       }
       __syncthreads();

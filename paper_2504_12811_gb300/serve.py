@@ -25,6 +25,10 @@ aaag_render_batch); this module only schedules.
 
 `plain_renderer` is the reference point: requests in arrival order, one at a
 time, each view rendered with aaag_render_frame on one stream.
+
+A request completes when its images (RGB and alpha of every view) have been
+copied to pinned host memory: latency = that completion seen by the host minus
+the arrival time.
 """
 from __future__ import annotations
 
@@ -46,11 +50,19 @@ class Slot:
     alpha_flat: torch.Tensor
     graphs: dict = field(default_factory=dict)
     urgent: torch.cuda.Stream = None     # high-priority stream for small requests
+    host_flat: torch.Tensor = None       # pinned host copy of the images (4 floats per pixel)
 
     def outputs(self, cam):
         hw = cam.width * cam.height
         return (self.rgb_flat[: 3 * hw].view(3, cam.height, cam.width),
                 self.alpha_flat[:hw].view(cam.height, cam.width))
+
+    def read_back(self, cam):
+        """Queue the copy of this view's images to the slot's pinned host
+        buffer on the current stream."""
+        hw = cam.width * cam.height
+        self.host_flat[: 3 * hw].copy_(self.rgb_flat[: 3 * hw], non_blocking=True)
+        self.host_flat[3 * hw: 4 * hw].copy_(self.alpha_flat[:hw], non_blocking=True)
 
 
 class Server:
@@ -71,7 +83,8 @@ class Server:
             self.slots.append(Slot(ws, torch.cuda.Stream(device=self.device),
                                    torch.empty(3 * max_width * max_height, device=device),
                                    torch.empty(max_width * max_height, device=device),
-                                   urgent=torch.cuda.Stream(device=self.device, priority=-1)))
+                                   urgent=torch.cuda.Stream(device=self.device, priority=-1),
+                                   host_flat=torch.empty(4 * max_width * max_height, pin_memory=True)))
         self.render_stream = torch.cuda.Stream(device=self.device)
         self.max_batch_views = max_batch_views
 
@@ -115,6 +128,9 @@ class Server:
         outs = [slot.outputs(cam) for slot, _, cam in views]
         aaag.aaag_render_batch([slot.ws.handle for slot, _, _ in views], [o[0].data_ptr() for o in outs],
                                [o[1].data_ptr() for o in outs], self.render_stream.cuda_stream)
+        with torch.cuda.stream(self.render_stream):
+            for slot, _, cam in views:
+                slot.read_back(cam)
         done = torch.cuda.Event()
         done.record(self.render_stream)
         return done
@@ -136,6 +152,9 @@ class Server:
         outs = [slot.outputs(cam) for slot, cam in zip(slots, req.cams)]
         aaag.aaag_render_batch([slot.ws.handle for slot in slots], [o[0].data_ptr() for o in outs],
                                [o[1].data_ptr() for o in outs], lead.cuda_stream)
+        with torch.cuda.stream(lead):
+            for slot, cam in zip(slots, req.cams):
+                slot.read_back(cam)
         done = torch.cuda.Event()
         done.record(lead)
         return done
@@ -277,6 +296,7 @@ def plain_renderer(scenes: dict, requests, max_width, max_height, pair_capacity,
     stream = torch.cuda.Stream(device=device)
     rgb = torch.empty(3 * max_width * max_height, device=device)
     alpha = torch.empty(max_width * max_height, device=device)
+    host = torch.empty(8 * max_width * max_height, pin_memory=True)   # two views
     prm = params if params is not None else aaag.make_params()
     # warm-up: one frame per shape
     for r in requests[:8]:
@@ -290,9 +310,13 @@ def plain_renderer(scenes: dict, requests, max_width, max_height, pair_capacity,
     for r in order:
         while time.perf_counter() - t0 < r.arrival:
             time.sleep(20e-6)
-        for cam in r.cams:
+        for v, cam in enumerate(r.cams):
             aaag.aaag_render_frame(structs[r.scene], aaag.make_camera(cam), prm, ws.handle, rgb.data_ptr(),
                                    alpha.data_ptr(), stream.cuda_stream)
+            hw = cam.width * cam.height
+            with torch.cuda.stream(stream):
+                host[4 * v * hw: 4 * v * hw + 3 * hw].copy_(rgb[: 3 * hw], non_blocking=True)
+                host[4 * v * hw + 3 * hw: 4 * (v + 1) * hw].copy_(alpha[:hw], non_blocking=True)
         stream.synchronize()
         lat[r.rid] = time.perf_counter() - t0 - r.arrival
     return [lat[r.rid] for r in requests]
