@@ -55,11 +55,13 @@ def parse():
     ap.add_argument("--no-hbm-large", action="store_true", help="skip preprocess and sort at 16M / 64M")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--capacity", type=int, default=48 << 20)
-    ap.add_argument("--serve", default="400:3,30:10",
+    ap.add_argument("--serve", default="40:10",
                     help="serving traces as rate_hz:seconds pairs ('' = skip serving)")
     ap.add_argument("--serve-warmup", type=float, default=0.0,
                     help="seconds at the start of each trace whose requests run but are not counted")
     ap.add_argument("--serve-policies", default="all", help="'all' or 'server,plain'")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving comparison and print its JSON (no frame timing)")
     ap.add_argument("--serve-capacity", type=int, default=1 << 28)
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     ap.add_argument("--sort-keys", type=int, default=0,
@@ -829,7 +831,12 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.sort_keys:
+    if args.serve_only:
+        import torch
+        from paper_2504_12811_gb300 import build as B
+        B.build()
+        print(json.dumps({"serving": run_serving(args, torch.device("cuda", 0))}), flush=True)
+    elif args.sort_keys:
         run_sort_only(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -96,7 +96,8 @@ enum StatSlot : int {
   kStatSortEpoch = 17,
   kStatFrameEpoch = 18,    // bumped by every frame's constants: tags the cull look-back words
   kStatRenderCounter = 19, // uint32 tile counter of the persistent render
-  kStatCount = 20
+  kStatBackwardCounter = 20, // uint32 tile counter of the persistent backward
+  kStatCount = 21
 };
 
 
@@ -160,6 +161,9 @@ aaag_status static_sort_wait_selftest(cudaStream_t st);
 int64_t cull_lookback_words(int64_t n, int64_t chunk_cap);
 aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st);
+// tiles of the frame in descending order of their pair counts into
+// ws->tile_order; resets the work counter of the persistent kernel that uses it
+aaag_status launch_tile_order(aaag_workspace* ws, uint32_t* counter, cudaStream_t st);
 aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, float* const* alpha, int n,
                                 cudaStream_t st);
 // Launch shapes that depend on the device: its SM count and the occupancy of
@@ -172,6 +176,7 @@ struct LaunchConfig {
   int cull_b_per_sm;     // cull_emit_kernel
   int sort_pass_per_sm;  // sort_pass_kernel
   int serve_per_sm;      // serve_render_kernel
+  int backward_per_sm;   // render_backward_kernel
 };
 const LaunchConfig& launch_config();
 // per translation unit: function attributes and occupancy of its kernels

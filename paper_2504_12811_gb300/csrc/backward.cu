@@ -307,19 +307,15 @@ struct BackwardBlend {
   }
 };
 
-__global__ void __launch_bounds__(kTilePixels, 2)
-render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
-                       const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
-                       const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
-                       const float* __restrict__ rgb,
-                       const float* __restrict__ drgb, const float* __restrict__ dalpha,
-                       const float* __restrict__ final_T, const uint32_t* __restrict__ n_blended,
-                       float4* __restrict__ grad, unsigned long long* __restrict__ stats) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem<IndexQueue>& s = *reinterpret_cast<TileSmem<IndexQueue>*>(smem_raw);
-  float* sacc = reinterpret_cast<float*>(smem_raw + kStageBytes);
-  const FrameConst fc = *fcp;
-  const int tile = blockIdx.x;
+// The backward of one tile (all threads of the block).
+__device__ __forceinline__ void backward_tile(TileSmem<IndexQueue>& s, float* sacc, int tile,
+                                              const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
+                                              const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
+                                              const uint4* __restrict__ aux, const FrameConst& fc,
+                                              const float* __restrict__ rgb, const float* __restrict__ drgb,
+                                              const float* __restrict__ dalpha, const float* __restrict__ final_T,
+                                              const uint32_t* __restrict__ n_blended, float4* __restrict__ grad,
+                                              unsigned long long* __restrict__ stats) {
   const int tx = tile % fc.tiles_x, ty = tile / fc.tiles_x;
   int lx, ly;
   tile_pixel(threadIdx.x, lx, ly);
@@ -371,6 +367,34 @@ render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restr
   const bool mismatch = in_image && bl.nblend != n_blended[p];
   const unsigned ball = __ballot_sync(0xffffffffu, mismatch);
   if ((threadIdx.x & 31) == 0 && ball) atomicAdd(&stats[kStatReplayMismatch], (unsigned long long)__popc(ball));
+}
+
+// Persistent: blocks take tiles from a work counter, longest first (the order
+// of tile_order_kernel, computed again from the frame's tile ranges).
+__global__ void __launch_bounds__(kTilePixels, 2)
+render_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
+                       const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
+                       const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
+                       const float* __restrict__ rgb,
+                       const float* __restrict__ drgb, const float* __restrict__ dalpha,
+                       const float* __restrict__ final_T, const uint32_t* __restrict__ n_blended,
+                       float4* __restrict__ grad, unsigned long long* __restrict__ stats,
+                       const uint32_t* __restrict__ order, uint32_t* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileSmem<IndexQueue>& s = *reinterpret_cast<TileSmem<IndexQueue>*>(smem_raw);
+  float* sacc = reinterpret_cast<float*>(smem_raw + kStageBytes);
+  __shared__ uint32_t s_item;
+  const FrameConst fc = *fcp;
+  const uint32_t n_tiles = (uint32_t)(fc.tiles_x * fc.tiles_y);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    __syncthreads();
+    if (item >= n_tiles) break;
+    backward_tile(s, sacc, (int)order[item], ranges, keys, vals, rec, aux, fc, rgb, drgb, dalpha, final_T,
+                  n_blended, grad, stats);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -587,21 +611,29 @@ preprocess_backward_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const
 
 }  // namespace
 
-void configure_backward(LaunchConfig&) {
+void configure_backward(LaunchConfig& c) {
   cudaFuncSetAttribute(render_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kBackwardSmemBytes);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_backward_kernel, kTilePixels, kBackwardSmemBytes);
+  c.backward_per_sm = std::max(1, per_sm);
 }
 
 aaag_status launch_render_backward(const SceneDev& s, aaag_workspace* ws, const float* rgb, const float* drgb,
                                    const float* dalpha, const aaag_grads* out, cudaStream_t st) {
   if (cudaMemsetAsync(ws->grad_acc, 0, (size_t)ws->n * sizeof(float4) * 4, st) != cudaSuccess)
     return check_launch("backward memset");
-  launch_config();   // function attributes of this device
+  const LaunchConfig& lc = launch_config();
   const int alt = ws->sorted_in_alt;
-  render_backward_kernel<<<(unsigned)ws->n_tiles, kTilePixels, kBackwardSmemBytes, st>>>(
+  uint32_t* counter = reinterpret_cast<uint32_t*>(ws->stats + kStatBackwardCounter);
+  aaag_status e = launch_tile_order(ws, counter, st);
+  if (e != AAAG_OK) return e;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)lc.sms * lc.backward_per_sm,
+                                                                          ws->n_tiles));
+  render_backward_kernel<<<grid, kTilePixels, kBackwardSmemBytes, st>>>(
       ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->aux, ws->fc_dev, rgb, drgb, dalpha, ws->final_T,
-      ws->n_blended, ws->grad_acc, ws->stats);
-  aaag_status e = check_launch("render_backward");
+      ws->n_blended, ws->grad_acc, ws->stats, ws->tile_order, counter);
+  e = check_launch("render_backward");
   if (e != AAAG_OK || s.n == 0) return e;
   const unsigned blocks = (unsigned)((s.n + 127) / 128);
   preprocess_backward_kernel<<<blocks, 128, 0, st>>>(s, ws->fc_dev, ws->counts, ws->grad_acc, out->means,

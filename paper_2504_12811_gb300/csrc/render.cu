@@ -54,7 +54,9 @@ struct ForwardBlend {
   __device__ __forceinline__ void begin_batch(uint32_t, int) {}
 };
 
-// Render one tile of one frame (all threads of the block).
+// Render one tile of one frame (all threads of the block).  EXACT: the frame
+// has neither ordering ablation.
+template <bool EXACT = false>
 __device__ __forceinline__ void render_tile(TileSmem<IndexQueue>& s, int tile, const uint2* __restrict__ ranges,
                                            const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                                            const Record* __restrict__ rec, const uint4* __restrict__ aux,
@@ -77,8 +79,8 @@ __device__ __forceinline__ void render_tile(TileSmem<IndexQueue>& s, int tile, c
   bl.nblend = 0;
   unsigned long long neval = 0;
   uint32_t nmis = 0, npass = 0;
-  traverse_tile<false>(s, ranges[tile], keys, vals, rec, aux, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f, bl,
-                       neval, nmis, npass);
+  traverse_tile<false, EXACT>(s, ranges[tile], keys, vals, rec, aux, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f,
+                              bl, neval, nmis, npass);
 
   if (in_image) {
     const size_t HW = (size_t)fc.W * fc.H;
@@ -108,26 +110,37 @@ __device__ __forceinline__ void render_tile(TileSmem<IndexQueue>& s, int tile, c
 
 // Tile order of the persistent render: tiles in descending order of their
 // pair counts (two buckets per octave), so that the longest tiles start first
-// and the short ones fill in behind them.  One block; also resets the work
+// and the short ones fill in behind them.  One block; the lanes of a warp that
+// fall into one bucket add to its counter with one atomic (a few buckets hold
+// most tiles, and per-lane atomics on them serialise).  Also resets the work
 // counter.
 __global__ void __launch_bounds__(1024)
 tile_order_kernel(const uint2* __restrict__ ranges, const FrameConst* __restrict__ fcp,
                   uint32_t* __restrict__ order, uint32_t* __restrict__ counter) {
-  __shared__ uint32_t base[64];
+  constexpr int kBuckets = 64;
+  __shared__ uint32_t base[kBuckets];
   const int n_tiles = fcp->tiles_x * fcp->tiles_y;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   auto bucket = [&](int t) {
+    if (t >= n_tiles) return kBuckets;                             // past the end
     const uint2 r = ranges[t];
     const uint32_t c = r.y - r.x + 1u;
     const int lz = 32 - __clz(c);                                   // 1..32
     const int half = lz >= 2 ? (int)((c >> (lz - 2)) & 1u) : 0;
-    return 63 - min(63, 2 * lz + half);                            // longest first
+    return kBuckets - 1 - min(kBuckets - 1, 2 * lz + half);        // longest first
   };
-  if (threadIdx.x < 64) base[threadIdx.x] = 0;
+  if (threadIdx.x < kBuckets) base[threadIdx.x] = 0;
   if (threadIdx.x == 0) *counter = 0;
   __syncthreads();
-  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&base[bucket(t)], 1u);
+  const int rounds = (n_tiles + (int)blockDim.x - 1) / (int)blockDim.x;   // the same for every lane
+  for (int r = 0; r < rounds; ++r) {
+    const int b = bucket(r * (int)blockDim.x + (int)threadIdx.x);
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    if (b < kBuckets && lane == __ffs(peers) - 1) atomicAdd(&base[b], (uint32_t)__popc(peers));
+  }
   __syncthreads();
-  if (threadIdx.x < 32) {   // exclusive scan of 64 counts, two per lane
+  if (threadIdx.x < 32) {   // exclusive scan of the 64 counts, two per lane
     const uint32_t c0 = base[2 * threadIdx.x], c1 = base[2 * threadIdx.x + 1];
     uint32_t incl = c0 + c1;
 #pragma unroll
@@ -140,10 +153,21 @@ tile_order_kernel(const uint2* __restrict__ ranges, const FrameConst* __restrict
     base[2 * threadIdx.x + 1] = excl + c0;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&base[bucket(t)], 1u)] = (uint32_t)t;
+  for (int r = 0; r < rounds; ++r) {
+    const int t = r * (int)blockDim.x + (int)threadIdx.x;
+    const int b = bucket(t);
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t first = 0;
+    if (b < kBuckets && lane == leader) first = atomicAdd(&base[b], (uint32_t)__popc(peers));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    if (b < kBuckets) order[first + (uint32_t)__popc(peers & lt)] = (uint32_t)t;
+  }
 }
 
 // Persistent: blocks take tiles in the order above from a work counter.
+// EXACT: compiled for frames without an ordering ablation.
+template <bool EXACT>
 __global__ void __launch_bounds__(kTilePixels, 3)
 render_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ keys,
               const uint32_t* __restrict__ vals, const Record* __restrict__ rec, const uint4* __restrict__ aux,
@@ -161,7 +185,7 @@ render_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ key
     const uint32_t item = s_item;
     __syncthreads();
     if (item >= n_tiles) break;
-    render_tile(s, (int)order[item], ranges, keys, vals, rec, aux, fc, rgb, alpha, final_T, n_blended, stats);
+    render_tile<EXACT>(s, (int)order[item], ranges, keys, vals, rec, aux, fc, rgb, alpha, final_T, n_blended, stats);
   }
 }
 
@@ -214,7 +238,8 @@ serve_render_kernel(const __grid_constant__ RenderBatch b, uint32_t* __restrict_
 }  // namespace
 
 void configure_render(LaunchConfig& c) {
-  cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kForwardSmemBytes);
+  cudaFuncSetAttribute(render_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kForwardSmemBytes);
+  cudaFuncSetAttribute(render_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kForwardSmemBytes);
   cudaFuncSetAttribute(serve_render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kForwardSmemBytes);
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_render_kernel, kTilePixels, kForwardSmemBytes);
@@ -255,17 +280,22 @@ aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, fl
   return check_launch("serve_render");
 }
 
+aaag_status launch_tile_order(aaag_workspace* ws, uint32_t* counter, cudaStream_t st) {
+  tile_order_kernel<<<1, 1024, 0, st>>>(ws->ranges, ws->fc_dev, ws->tile_order, counter);
+  return check_launch("tile_order");
+}
+
 aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStream_t st) {
   const LaunchConfig& lc = launch_config();
   const int alt = ws->sorted_in_alt;
   uint32_t* counter = reinterpret_cast<uint32_t*>(ws->stats + kStatRenderCounter);
-  tile_order_kernel<<<1, 1024, 0, st>>>(ws->ranges, ws->fc_dev, ws->tile_order, counter);
-  aaag_status e = check_launch("tile_order");
+  aaag_status e = launch_tile_order(ws, counter, st);
   if (e != AAAG_OK) return e;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)lc.sms * lc.serve_per_sm, ws->n_tiles));
-  render_kernel<<<grid, kTilePixels, kForwardSmemBytes, st>>>(ws->ranges, ws->keys[alt], ws->vals[alt], ws->records,
-                                                               ws->aux, ws->fc_dev, rgb, alpha, ws->final_T,
-                                                               ws->n_blended, ws->stats, ws->tile_order, counter);
+  auto kernel = (ws->fc.flags & (AAAG_FLAG_NO_RESORT | AAAG_FLAG_KBUFFER)) ? render_kernel<false> : render_kernel<true>;
+  kernel<<<grid, kTilePixels, kForwardSmemBytes, st>>>(ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->aux,
+                                                        ws->fc_dev, rgb, alpha, ws->final_T, ws->n_blended, ws->stats,
+                                                        ws->tile_order, counter);
   return check_launch("render");
 }
 

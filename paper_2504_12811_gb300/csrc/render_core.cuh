@@ -310,8 +310,9 @@ __device__ __forceinline__ void release_rounds(SmemQueue<Q>& q, Blender& bl, Wan
 //   void end_batch(uint32_t b0, int cnt);            block-converged, after a batch
 // The arithmetic, and so every blend decision, is the same either way.
 // npass counts this pixel's passes beyond the first (depth peeling); nmis the
-// early releases of the bounded-buffer ablation.
-template <bool CONVERGENT, class Blender>
+// early releases of the bounded-buffer ablation.  EXACT: the frame has neither
+// ordering ablation (the flags are then known at compile time).
+template <bool CONVERGENT, bool EXACT = false, class Blender>
 __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>& sm, const uint2 range, const uint32_t* __restrict__ keys,
                                               const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
                                               const uint4* __restrict__ aux, const FrameConst& fc, int tile_x,
@@ -322,8 +323,8 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
   const uint32_t wbit = 1u << (threadIdx.x >> 5);
   // ablations: blend in pair order (no re-sort); release only when the
   // buffer is full (no release by key)
-  const bool resort = !(fc.flags & AAAG_FLAG_NO_RESORT);
-  const bool by_key = !(fc.flags & AAAG_FLAG_KBUFFER);
+  const bool resort = EXACT || !(fc.flags & AAAG_FLAG_NO_RESORT);
+  const bool by_key = EXACT || !(fc.flags & AAAG_FLAG_KBUFFER);
   const bool peel = resort && by_key;   // exact order: defer instead of releasing early
   const float kInf = __int_as_float(0x7f800000);
   constexpr uint32_t kNone = 0xffffffffu;
@@ -523,9 +524,9 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
                     }
                   }
                 }
+                if (bl.done) break;   // blends are the only change of done
               }
             }
-            if (bl.done) break;
           }
         };
         if (lo == -kInf) {
