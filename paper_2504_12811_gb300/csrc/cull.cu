@@ -210,15 +210,19 @@ __device__ __forceinline__ bool tile_needed(float4 t1, float4 t2, float4 t3, flo
 
 // Depth key of a (Gaussian, tile) pair: the ray maximum of a pixel lies at
 // t* = G.d / |d|^2 (render_core.cuh), with d affine in the pixel centre and
-// G the Gaussian's constant vector.  Over the tile's pixel centres
-// (tile-relative x, y in [0.5, 15.5]) G.d is affine, so its minimum is at a
-// corner, and |d|^2 is convex, so its maximum is at a corner: when the
-// smallest corner value of G.d is positive, min G.d / max |d|^2 bounds t* from
-// below on every ray of the tile.  Lowered by 1e-5 relative (float32 rounding
-// of the render's t*), quantised like the Gaussian's own key and rounded down;
-// 0 (the smallest key) when no bound results.  The pair key is the larger of
-// this and the Gaussian's key: both are lower bounds, and a tighter one lets
-// more contributors blend at once instead of waiting in the per-pixel queue.
+// G the Gaussian's constant vector.  Over the rectangle of the tile's pixel
+// centres (tile-relative x, y in [0.5, 15.5]) the smallest t* is found at a
+// corner: when every corner has G.d > 0, let m be the smallest corner value
+// of t*; then h = G.d - m |d|^2 is concave (affine minus a convex quadratic
+// with m > 0) and non-negative at the corners, so non-negative on the whole
+// rectangle, i.e. t* >= m at every pixel of the tile, and m is attained.  The
+// bound is lowered by the float32 rounding of either side (the render's t*
+// and this one): 1e-5 of sum |G_i d_i| / |d|^2, which is at least 1e-5 t* and
+// grows where G.d cancels, plus 1e-6; quantised like the Gaussian's own key
+// and rounded down; 0 (the smallest key) when no bound results.  The pair key
+// is the larger of this and the Gaussian's key: both are lower bounds, and a
+// tighter one lets more contributors blend at once instead of waiting in the
+// per-pixel queue.
 __device__ __forceinline__ uint32_t tile_depth_key(float4 t1, float4 t2, float4 t3, const FrameConst& fc,
                                                    int tx, int ty) {
   const float cxm = fc.cx - (float)(tx * kTile), cym = fc.cy - (float)(ty * kTile);
@@ -227,18 +231,18 @@ __device__ __forceinline__ uint32_t tile_depth_key(float4 t1, float4 t2, float4 
   const float3 Wv = fc.fy * A2 + cym * T3;
   const float3 D0 = cross3(Uv, Wv), Dx = cross3(Wv, T3), Dy = cross3(T3, Uv);
   const float3 G = (fc.fx * fc.fy) * (t1.w * cross3(A2, T3) + t2.w * cross3(T3, A1) + t3.w * cross3(A1, A2));
-  float nmin = 3.0e38f, qmax = 0.0f;
+  float z = 3.0e38f;
+  bool ok = true;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const float x = (k & 1) ? 15.5f : 0.5f, y = (k & 2) ? 15.5f : 0.5f;
     const float3 d = D0 + x * Dx + y * Dy;
-    nmin = fminf(nmin, dot3(G, d));
-    qmax = fmaxf(qmax, dot3(d, d));
+    const float gd = dot3(G, d), dd = dot3(d, d);
+    const float mag = fabsf(G.x * d.x) + fabsf(G.y * d.y) + fabsf(G.z * d.z);
+    ok = ok && gd > 0.0f && dd > 0.0f;
+    z = fminf(z, (gd - 1e-5f * mag) / dd - 1e-6f);
   }
-  if (!(nmin > 0.0f) || !(qmax > 0.0f)) return 0u;
-  float z = nmin / qmax;
-  z -= 1e-5f * z + 1e-6f;
-  if (!(z > fc.znear)) return 0u;
+  if (!ok || !(z > fc.znear)) return 0u;
   const uint32_t dmax = (fc.depth_bits >= 32) ? 0xffffffffu : ((1u << fc.depth_bits) - 1u);
   return min((__float_as_uint(z) - fc.znear_bits) >> fc.depth_shift, dmax);
 }
