@@ -183,3 +183,4 @@ def test_tile_depth_bound_corner_rule_on_random_planes():
         assert t.min() >= m - 1e-12 * abs(m)
         hit += 1
     assert hit > 500
+
