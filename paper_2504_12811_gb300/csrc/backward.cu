@@ -49,6 +49,27 @@ constexpr int kAccStride = kMoments + 1;   // odd: slot-major rows fall in disti
 constexpr size_t kBackwardSmemBytes = kStageBytes + sizeof(float) * kAccStride * kTilePixels;
 constexpr int kMinGroup = 24;   // lanes releasing one Gaussian in a round that are summed before the atomics
 
+// One level of the halving reduce-scatter of end_item: M values per lane
+// (positions 0 .. M-1) become (M + 1) / 2, exchanged with lane ^ H.
+template <int H, int M>
+__device__ __forceinline__ void halving_level(float* v, int lane, int& off, int& left) {
+  constexpr int kHalf = (M + 1) / 2;
+  const bool upper = (lane & H) != 0;
+#pragma unroll
+  for (int i = 0; i < kHalf; ++i) {
+    const float lo = v[i], hi = i + kHalf < M ? v[i + kHalf] : 0.0f;
+    const float send = upper ? lo : hi;
+    const float keep = upper ? hi : lo;
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, H);
+  }
+  if (upper) {
+    off += kHalf;
+    left = max(left - kHalf, 0);
+  } else {
+    left = min(left, kHalf);
+  }
+}
+
 struct BackwardBlend {
   using Queue = IndexQueue;
   const StageSmem* st;
@@ -230,29 +251,28 @@ struct BackwardBlend {
     const float4 c = __ldg(reinterpret_cast<const float4*>(rec + st->gid[ev.k]) + 3);
     if (moments(a, c, st->a[ev.k].w, ev.n0, ev.n1, ev.n2, ev.d0, ev.d1, ev.d2, ev.inv, ev.rho2, acc)) has = true;
   }
-  // Warp reduction of the 22 moments of item k by halving exchanges: at each
-  // level every lane keeps one half of its values and receives its partner's
-  // copy of that half, so after five levels lane i holds the warp total of
-  // moment i (31 shuffles instead of 5 per moment); lanes 0..21 then add
-  // their moment to slot k in one instruction.
+  // Warp reduction of the 22 moments of item k by halving exchanges
+  // (reduce-scatter): at each level a lane keeps one half of its values and
+  // receives its partner's copy of that half, so the value count per lane
+  // goes 22 -> 11 -> 6 -> 3 -> 2 -> 1 (23 shuffles; padding to 32 values
+  // would take 31).  Position p of a lane's kept upper half stands for
+  // position p + half before the level; a lane ends with the warp total of
+  // one moment, or of nothing when its path ran past the real positions
+  // (22 of the 32 lanes hold one moment each).  Those lanes add it to slot k.
   __device__ __forceinline__ void end_item(int k) {
     const unsigned any = __ballot_sync(0xffffffffu, has);
     if (!any) return;
     const int lane = threadIdx.x & 31;
-    float v[32];
+    float v[kMoments];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = (i < kMoments && has) ? acc[i] : 0.0f;
-#pragma unroll
-    for (int h = 16; h > 0; h >>= 1) {
-      const bool upper = (lane & h) != 0;
-#pragma unroll
-      for (int i = 0; i < h; ++i) {
-        const float send = upper ? v[i] : v[i + h];
-        const float keep = upper ? v[i + h] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
-      }
-    }
-    if (lane < kMoments && v[0] != 0.0f) atomicAdd(&sacc[k * kAccStride + lane], v[0]);
+    for (int i = 0; i < kMoments; ++i) v[i] = has ? acc[i] : 0.0f;
+    int off = 0, left = kMoments;   // moment held at position 0; real positions left
+    halving_level<16, kMoments>(v, lane, off, left);
+    halving_level<8, (kMoments + 1) / 2>(v, lane, off, left);
+    halving_level<4, (kMoments + 3) / 4>(v, lane, off, left);
+    halving_level<2, (kMoments + 7) / 8>(v, lane, off, left);
+    halving_level<1, (kMoments + 15) / 16>(v, lane, off, left);
+    if (left > 0 && v[0] != 0.0f) atomicAdd(&sacc[k * kAccStride + off], v[0]);
 #pragma unroll
     for (int i = 0; i < kMoments; ++i) acc[i] = 0.0f;
     has = false;

@@ -355,12 +355,16 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
     q.order = 0ull;
     q.used = 0u;
     for (uint32_t b0 = start; b0 < range.y; b0 += kTilePixels) {
+      // close the pass once no pair from here on can hold a contributor below hi
       if constexpr (!CONVERGENT) {
-        // close the pass once no pair from here on can hold a contributor below hi
         if (open && hi < kInf && decode_depth(keys[b0], fc) >= hi) {
           while (q.n > 0 && !bl.done) q.release(bl);
           open = false;
         }
+      } else {
+        const bool close = open && hi < kInf && decode_depth(keys[b0], fc) >= hi;
+        release_rounds(q, bl, [&] { return close && q.n > 0 && !bl.done; });
+        if (close) open = false;
       }
       if (__syncthreads_count(open && !bl.done) == 0) break;
       const uint32_t j = b0 + threadIdx.x;
