@@ -223,14 +223,26 @@ __device__ __forceinline__ bool tile_needed(float4 t1, float4 t2, float4 t3, flo
 // is the larger of this and the Gaussian's key: both are lower bounds, and a
 // tighter one lets more contributors blend at once instead of waiting in the
 // per-pixel queue.
-__device__ __forceinline__ uint32_t tile_depth_key(float4 t1, float4 t2, float4 t3, const FrameConst& fc,
-                                                   int tx, int ty) {
+struct KeyGeom {
+  float3 A1, A2, T3;   // rows of T_view without their last column
+  float3 G;            // fx fy adj(A) mu_v: t* = G.d / |d|^2
+};
+
+__device__ __forceinline__ KeyGeom key_geom(float4 t1, float4 t2, float4 t3, const FrameConst& fc) {
+  KeyGeom k;
+  k.A1 = f3(t1.x, t1.y, t1.z);
+  k.A2 = f3(t2.x, t2.y, t2.z);
+  k.T3 = f3(t3.x, t3.y, t3.z);
+  k.G = (fc.fx * fc.fy) * (t1.w * cross3(k.A2, k.T3) + t2.w * cross3(k.T3, k.A1) + t3.w * cross3(k.A1, k.A2));
+  return k;
+}
+
+__device__ __forceinline__ uint32_t tile_depth_key(const KeyGeom& kg, const FrameConst& fc, int tx, int ty) {
   const float cxm = fc.cx - (float)(tx * kTile), cym = fc.cy - (float)(ty * kTile);
-  const float3 T3 = f3(t3.x, t3.y, t3.z), A1 = f3(t1.x, t1.y, t1.z), A2 = f3(t2.x, t2.y, t2.z);
-  const float3 Uv = fc.fx * A1 + cxm * T3;
-  const float3 Wv = fc.fy * A2 + cym * T3;
+  const float3 T3 = kg.T3, G = kg.G;
+  const float3 Uv = fc.fx * kg.A1 + cxm * T3;
+  const float3 Wv = fc.fy * kg.A2 + cym * T3;
   const float3 D0 = cross3(Uv, Wv), Dx = cross3(Wv, T3), Dy = cross3(T3, Uv);
-  const float3 G = (fc.fx * fc.fy) * (t1.w * cross3(A2, T3) + t2.w * cross3(T3, A1) + t3.w * cross3(A1, A2));
   float z = 3.0e38f;
   bool ok = true;
 #pragma unroll
@@ -307,7 +319,6 @@ cull_emit_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
   const int64_t nch = min((int64_t)*n_chunks_dev, chunk_cap);
   const int64_t n_tiles = (nch + kChunkTile - 1) / kChunkTile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
   volatile unsigned long long* lb = lookback;
   for (;;) {
     if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(counter, 1u);
@@ -364,34 +375,31 @@ cull_emit_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
     __syncthreads();
     unsigned long long wbase = s_prefix;
     for (int w = 0; w < warp; ++w) wbase += s_wcount[w];
-    // the warp writes its chunks one after the other, one lane per pair
-    unsigned pending = __ballot_sync(0xffffffffu, m != 0u);
-    while (pending) {
-      const int i = __ffs(pending) - 1;
-      pending &= pending - 1u;
-      const uint32_t mi = __shfl_sync(0xffffffffu, m, i);
-      const uint32_t gi = __shfl_sync(0xffffffffu, g, i);
-      const uint32_t ax = __shfl_sync(0xffffffffu, a.x, i), ay = __shfl_sync(0xffffffffu, a.y, i);
-      const uint32_t aw = __shfl_sync(0xffffffffu, a.w, i);
-      const int li = __shfl_sync(0xffffffffu, local, i);
-      const uint32_t before = __shfl_sync(0xffffffffu, incl - cnt, i);
-      if ((mi >> lane) & 1u) {
-        int tx0, ty0, tx1, ty1;
-        unpack_rect(make_uint4(ax, ay, 0u, 0u), tx0, ty0, tx1, ty1);
-        const int nx = tx1 - tx0 + 1;
-        const int j = li * 32 + lane;
-        const uint64_t at = wbase + before + (uint64_t)__popc(mi & lt);
-        if (at < (uint64_t)capacity) {
-          const int txi = tx0 + j % nx, tyi = ty0 + j / nx;
-          const uint32_t t = (uint32_t)(tyi * fc.tiles_x + txi);
-          uint32_t dk = aw;
-          if (!(fc.flags & kMeanDepthKeyFlags)) {
-            const float4* r = reinterpret_cast<const float4*>(rec + gi);
-            dk = max(dk, tile_depth_key(__ldg(r + 0), __ldg(r + 1), __ldg(r + 2), fc, txi, tyi));
-          }
-          keys[at] = (t << fc.depth_bits) | dk;
-          vals[at] = gi;
-        }
+    // every lane writes the pairs of its own chunk, in tile order: the warp
+    // takes as many rounds as the largest chunk has tiles (a warp of small
+    // Gaussians' chunks finishes in a few), and each lane loads its
+    // Gaussian's rows and the parts of its key bound that do not depend on
+    // the tile once
+    if (m != 0u) {
+      int tx0, ty0, tx1, ty1;
+      unpack_rect(a, tx0, ty0, tx1, ty1);
+      const int nx = tx1 - tx0 + 1;
+      const bool tile_keys = !(fc.flags & kMeanDepthKeyFlags);
+      KeyGeom kg;
+      if (tile_keys) {
+        const float4* r = reinterpret_cast<const float4*>(rec + g);
+        kg = key_geom(__ldg(r + 0), __ldg(r + 1), __ldg(r + 2), fc);
+      }
+      uint64_t at = wbase + (incl - cnt);
+      for (uint32_t mm = m; mm != 0u; mm &= mm - 1u, ++at) {
+        if (at >= (uint64_t)capacity) break;
+        const int j = local * 32 + (__ffs(mm) - 1);
+        const int txi = tx0 + j % nx, tyi = ty0 + j / nx;
+        const uint32_t t = (uint32_t)(tyi * fc.tiles_x + txi);
+        uint32_t dk = a.w;
+        if (tile_keys) dk = max(dk, tile_depth_key(kg, fc, txi, tyi));
+        keys[at] = (t << fc.depth_bits) | dk;
+        vals[at] = g;
       }
     }
     __syncthreads();
