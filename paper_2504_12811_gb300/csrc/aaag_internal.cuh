@@ -175,6 +175,7 @@ struct LaunchConfig {
   int cull_a_per_sm;     // chunk_offsets_kernel
   int cull_b_per_sm;     // cull_emit_kernel
   int sort_pass_per_sm;  // sort_pass_kernel
+  int sort_wide_per_sm;  // sort_pass_kernel, 12 keys per thread
   int serve_per_sm;      // serve_render_kernel
   int backward_per_sm;   // render_backward_kernel
 };
@@ -193,7 +194,8 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
                                 int key_bits, uint32_t* hist, uint32_t* counters,
                                 unsigned long long* lookback, int64_t lookback_words,
                                 unsigned long long* epoch, unsigned long long* timeout_flag,
-                                int* result_in_alt, cudaStream_t st, bool prepared = false);
+                                int* result_in_alt, cudaStream_t st, bool prepared = false,
+                                bool n_exact = false);
 size_t radix_sort_scratch(int64_t n_max);
 
 // ---------------------------------------------------------------------------

@@ -520,7 +520,7 @@ aaag_status aaag_radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, 
   int alt = 0;
   const int64_t lb_words = std::max<int64_t>(sort_max_tiles(n), 1) * 256;
   const aaag_status e = radix_sort_device_n(keys, vals, keys_alt, vals_alt, n_dev, n, key_bits, hist, counters,
-                                            lookback, lb_words, epoch, timeout, &alt, stream);
+                                            lookback, lb_words, epoch, timeout, &alt, stream, false, true);
   *result_in_alt = alt;
   return e;
 }

@@ -490,8 +490,10 @@ preprocess_test_kernel(SceneDev s, const FrameConst* __restrict__ fcp, uint32_t*
 }
 
 // Phase 2: full preprocessing of the candidates (grid-stride over the count
-// left in device memory by phase 1).
-__global__ void __launch_bounds__(256, 3)
+// left in device memory by phase 1).  Two blocks per SM: with the registers
+// of three (85 per thread) the kernel spilled and ran 9% slower at 16M
+// Gaussians; four were slower still.
+__global__ void __launch_bounds__(256, 2)
 preprocess_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const uint32_t* __restrict__ cand,
                   const uint32_t* __restrict__ n_cand, Record* __restrict__ rec, uint4* __restrict__ aux,
                   uint32_t* __restrict__ chunks, unsigned long long* __restrict__ stats) {

@@ -3,7 +3,7 @@
 // minor).
 //
 // Onesweep structure: one histogram kernel reads every key once and counts
-// all digit positions; then one kernel per 8-bit digit ranks a 1024- or 2048-key tile
+// all digit positions; then one kernel per 8-bit digit ranks a 1024-, 2048- or 3072-key tile
 // per block (warp-level multisplit with __match_any_sync, preserving input
 // order), publishes its per-digit counts, resolves the exclusive prefix of
 // earlier tiles by decoupled look-back, and scatters through shared memory.
@@ -88,9 +88,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
   return pre + x - v;
 }
 
+template <int TILE>
 struct SortSmem {
-  uint32_t keys[kSortTileKeys];
-  uint32_t vals[kSortTileKeys];
+  uint32_t keys[TILE];
+  uint32_t vals[TILE];
   uint32_t warp[kSortThreads / 32][kRadix];   // per-warp digit counts -> prefixes
   uint32_t digit_start[kRadix];               // block-local digit starts
   uint32_t global[kRadix];                    // global start of this block's digits
@@ -142,8 +143,8 @@ __device__ __forceinline__ uint32_t digit_lookback(const volatile unsigned long 
 }
 
 // Tiles of ITEMS keys per thread, taken in order from the pass counter.
-template <int ITEMS>
-__device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __restrict__ keys_in,
+template <int ITEMS, int TILE>
+__device__ __forceinline__ void sort_pass_tiles(SortSmem<TILE>& sm, const uint32_t* __restrict__ keys_in,
                                                 const uint32_t* __restrict__ vals_in,
                                                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                 int64_t n, int shift, uint32_t gofs, uint32_t* __restrict__ counter,
@@ -209,16 +210,11 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __
     }
     const uint32_t local_start = block_exclusive_scan_256(count, s_tmp);
     s_digit_start[tid] = local_start;
-
-    uint32_t prefix = 0;
-    if (tile > 0) {
-      prefix = digit_lookback(lb, tile, tid, tag, timeout_flag);
-      lb[tile * kRadix + tid] = tag | kFlagPrefix | (unsigned long long)(prefix + count);
-    }
-    s_global[tid] = gofs + prefix;
     __syncthreads();
 
-    // ---- scatter into shared memory in digit order, then to global memory
+    // ---- scatter into shared memory in digit order (needs only this tile's
+    // counts, so it runs before the look-back: the predecessors get that
+    // much longer to publish their prefixes), then to global memory
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const uint32_t d = (k[j] >> shift) & 0xffu;
@@ -226,6 +222,13 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem& sm, const uint32_t* __
       s_keys[pos] = k[j];
       s_vals[pos] = v[j];
     }
+
+    uint32_t prefix = 0;
+    if (tile > 0) {
+      prefix = digit_lookback(lb, tile, tid, tag, timeout_flag);
+      lb[tile * kRadix + tid] = tag | kFlagPrefix | (unsigned long long)(prefix + count);
+    }
+    s_global[tid] = gofs + prefix;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -258,6 +261,13 @@ __device__ __forceinline__ int sort_items_for(int64_t n) {
   return n >= kSortWideKeys / 2 ? 8 : 4;
 }
 
+// WIDE: tiles of 12 keys per thread (3072), for sorts of at least
+// kSortWideMin keys whose size is known on the host; its 77 registers leave
+// three blocks per SM, so it is a kernel of its own (the other keeps four).
+constexpr int kWideItems = 12;
+constexpr int64_t kSortWideMin = 4 << 20;
+
+template <bool WIDE>
 __global__ void __launch_bounds__(kSortThreads)
 sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                  uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
@@ -266,19 +276,23 @@ sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
                  unsigned long long* __restrict__ lookback,
                  const unsigned long long* __restrict__ epoch_dev,
                  unsigned long long* __restrict__ timeout_flag) {
-  __shared__ SortSmem sm;
+  __shared__ SortSmem<(WIDE ? kWideItems : kSortItems) * kSortThreads> sm;
   const int64_t n = min((int64_t)*n_dev, n_max);
   const unsigned long long epoch = ((*epoch_dev) * 8ull + (unsigned long long)pass) & 0xffffffffull;
   const unsigned long long tag = epoch << 32;
   // global exclusive offset of digit `threadIdx.x` for this pass
   const uint32_t gofs = block_exclusive_scan_256(hist[pass * kRadix + threadIdx.x], sm.tmp);
-  const int items = sort_items_for(n);
-  if (items == 8)
-    sort_pass_tiles<8>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
-                       timeout_flag);
-  else
-    sort_pass_tiles<4>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
-                       timeout_flag);
+  if constexpr (WIDE) {
+    sort_pass_tiles<kWideItems>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback,
+                                tag, timeout_flag);
+  } else {
+    if (sort_items_for(n) == 8)
+      sort_pass_tiles<8>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
+                         timeout_flag);
+    else
+      sort_pass_tiles<4>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
+                         timeout_flag);
+  }
 }
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev,
@@ -296,8 +310,11 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t*
 
 void configure_sort(LaunchConfig& c) {
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_pass_kernel, kSortThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_pass_kernel<false>, kSortThreads, 0);
   c.sort_pass_per_sm = std::max(1, per_sm);
+  per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_pass_kernel<true>, kSortThreads, 0);
+  c.sort_wide_per_sm = std::max(1, per_sm);
 }
 
 size_t radix_sort_scratch(int64_t n_max) {
@@ -311,7 +328,7 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
                                 int key_bits, uint32_t* hist, uint32_t* counters,
                                 unsigned long long* lookback, int64_t lookback_words,
                                 unsigned long long* epoch, unsigned long long* timeout_flag,
-                                int* result_in_alt, cudaStream_t st, bool prepared) {
+                                int* result_in_alt, cudaStream_t st, bool prepared, bool n_exact) {
   const int passes = (key_bits + 7) / 8;
   *result_in_alt = passes & 1;
   if (n_max <= 0 || passes == 0) {
@@ -325,13 +342,19 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
                                                            lookback_words, epoch);
   aaag_status e = check_launch("sort_histogram");
   if (e != AAAG_OK) return e;
-  const int64_t grid = std::min<int64_t>(sort_max_tiles(n_max), (int64_t)lc.sms * lc.sort_pass_per_sm);
+  // wide tiles when the count is known to be large (n_max is the count
+  // itself, not a capacity)
+  const bool wide = n_exact && n_max >= kSortWideMin;
+  const int64_t tiles = wide ? (n_max + kWideItems * kSortThreads - 1) / (kWideItems * kSortThreads)
+                             : sort_max_tiles(n_max);
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)lc.sms * (wide ? lc.sort_wide_per_sm : lc.sort_pass_per_sm));
+  auto pass_kernel = wide ? sort_pass_kernel<true> : sort_pass_kernel<false>;
   uint32_t* kin = keys;
   uint32_t* vin = vals;
   uint32_t* kout = keys_alt;
   uint32_t* vout = vals_alt;
   for (int p = 0; p < passes; ++p) {
-    sort_pass_kernel<<<(unsigned)grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_dev, n_max, p, hist,
+    pass_kernel<<<(unsigned)grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_dev, n_max, p, hist,
                                                                counters + p, lookback, epoch, timeout_flag);
     e = check_launch("sort_pass");
     if (e != AAAG_OK) return e;
