@@ -151,6 +151,33 @@ namespace aaag {
 void set_error(const char* fmt, ...);
 aaag_status check_launch(const char* what);
 
+// Programmatic dependent launch along the frame's chain of kernels: each is
+// launched with programmatic stream serialisation, so the next kernel's grid
+// is set up while the previous one drains; its blocks start with pdl_begin,
+// which waits until the previous grid has completed and its writes are
+// visible (exactly the ordering of a plain launch) and then lets the next
+// grid launch.  Without a programmatic dependency the wait returns at once.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                           Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // kernel launchers (one per translation unit)
 aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_t st);
 aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st);

@@ -197,17 +197,20 @@ __global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
 // Frame constants are a kernel parameter here and device memory for every
 // other kernel of the frame: a captured frame graph is re-aimed at a new
 // camera by updating this one node.
-// Frame constants to device memory; the frame epoch tags this frame's cull
-// look-back words with its low 24 bits.  When those wrap to zero every word is
-// cleared (an unpublished word), so that a word left from 2^24 frames earlier
-// can never pass for one of this frame.
-__global__ void set_frame_kernel(FrameConst* dst, FrameConst v, unsigned long long* frame_epoch,
+// Frame constants to device memory, and the per-frame statistics reset (the
+// words below kStatFrameReset; the sort epoch and the others stay).  The frame
+// epoch tags this frame's cull look-back words with its low 24 bits.  When
+// those wrap to zero every word is cleared (an unpublished word), so that a
+// word left from 2^24 frames earlier can never pass for one of this frame.
+__global__ void set_frame_kernel(FrameConst* dst, FrameConst v, unsigned long long* stats,
                                  unsigned long long* cull_lb, long long lb_words) {
+  pdl_begin();
   __shared__ unsigned long long e;
+  if (threadIdx.x < kStatFrameReset) stats[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) {
     *dst = v;
-    e = *frame_epoch + 1ull;
-    *frame_epoch = e;
+    e = stats[kStatFrameEpoch] + 1ull;
+    stats[kStatFrameEpoch] = e;
   }
   __syncthreads();
   if ((e & 0xffffffull) == 0ull)
@@ -408,13 +411,10 @@ aaag_status aaag_preprocess(const aaag_scene* scene, const aaag_camera* camera, 
   ws->have_frame = true;
   ws->pairs_unsorted = false;
   ws->sorted_in_alt = 0;
-  set_frame_kernel<<<1, 256, 0, stream>>>(ws->fc_dev, fc, ws->stats + kStatFrameEpoch, ws->cull_lookback,
+  set_frame_kernel<<<1, 256, 0, stream>>>(ws->fc_dev, fc, ws->stats, ws->cull_lookback,
                                           (long long)ws->n_cull_words);
   e = check_launch("set_frame");
   if (e != AAAG_OK) return e;
-  // reset per-frame statistics (keep the sort epoch)
-  if (cudaMemsetAsync(ws->stats, 0, kStatFrameReset * 8, stream) != cudaSuccess)
-    return check_launch("preprocess memset");
   return launch_preprocess(scene_dev(scene), ws, stream);
 }
 
@@ -697,10 +697,10 @@ aaag_status aaag_graph_launch(aaag_graph* g, const aaag_camera* camera, cudaStre
   aaag_status e = make_frame(camera, g->has_params ? &g->params : nullptr, g->sh_degree, ws, &fc);
   if (e != AAAG_OK) return e;
   FrameConst* dst = ws->fc_dev;
-  unsigned long long* epoch = ws->stats + kStatFrameEpoch;
+  unsigned long long* stats = ws->stats;
   unsigned long long* cull_lb = ws->cull_lookback;
   long long lb_words = (long long)ws->n_cull_words;
-  void* args[5] = {&dst, &fc, &epoch, &cull_lb, &lb_words};
+  void* args[5] = {&dst, &fc, &stats, &cull_lb, &lb_words};
   cudaKernelNodeParams p = g->frame_params;
   p.kernelParams = args;
   p.extra = nullptr;

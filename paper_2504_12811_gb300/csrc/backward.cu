@@ -379,7 +379,7 @@ __device__ __forceinline__ void backward_tile(TileSmem<IndexQueue>& s, float* sa
   }
   bl.Tfinal = Tf;
   bl.done = !in_image;
-  unsigned long long neval = 0;
+  uint32_t neval = 0;   // evaluations of this pixel (far below 2^32 per tile)
   uint32_t nmis = 0, npass = 0;
   __syncthreads();
   traverse_tile<true>(s, ranges[tile], keys, vals, rec, aux, fc, tx, ty, bl.x, bl.y, bl, neval, nmis, npass);

@@ -8,7 +8,8 @@
 // look-back over tiles taken in order from an atomic counter:
 //   A. chunk_offsets_kernel: tiles of 2048 Gaussians; exclusive scan of the
 //      per-Gaussian chunk counts (written by K1) -> each Gaussian's first
-//      chunk, and each Gaussian writes its index into its chunks' owner slots.
+//      chunk, and each Gaussian writes its index into its chunks' owner slots
+//      (it also prepares K3's counters and empties K4's tile ranges).
 //   B. cull_test_kernel: one warp per chunk (grid-stride), one lane per tile;
 //      the ballot of the needed tiles is stored per chunk.
 //   C. cull_emit_kernel: tiles of 256 chunks; the tile's pair count is
@@ -123,7 +124,11 @@ chunk_offsets_kernel(const uint32_t* __restrict__ counts, int64_t n, int64_t chu
                      uint32_t* __restrict__ offsets, uint32_t* __restrict__ owner,
                      unsigned long long* __restrict__ lookback, unsigned long long* __restrict__ stats,
                      uint32_t* __restrict__ n_chunks_clipped, uint32_t* __restrict__ sort_hist,
-                     uint32_t* __restrict__ sort_counters) {
+                     uint32_t* __restrict__ sort_counters, uint2* __restrict__ ranges, int n_ranges) {
+  pdl_begin();
+  // empty tile ranges for K4, which writes only the tiles that hold pairs
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_ranges; i += gridDim.x * blockDim.x)
+    ranges[i] = make_uint2(0u, 0u);
   __shared__ unsigned long long s_wsum[kWarps];
   __shared__ unsigned long long s_prefix;
   __shared__ int64_t s_tile;
@@ -266,6 +271,7 @@ cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
                  const uint32_t* __restrict__ owner, const uint32_t* __restrict__ chunk_offsets,
                  const uint32_t* __restrict__ n_chunks_dev, int64_t chunk_cap, uint32_t* __restrict__ masks,
                  unsigned long long* __restrict__ stats) {
+  pdl_begin();
   const FrameConst fc = *fcp;
   const int64_t nch = min((int64_t)*n_chunks_dev, chunk_cap);
   const int lane = threadIdx.x & 31;
@@ -310,6 +316,7 @@ cull_emit_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity,
                  unsigned long long* __restrict__ lookback, unsigned long long* __restrict__ stats,
                  uint32_t* __restrict__ n_pairs_clipped) {
+  pdl_begin();
   __shared__ uint32_t s_wcount[kWarps];
   __shared__ unsigned long long s_prefix;
   __shared__ int64_t s_tile;
@@ -434,20 +441,20 @@ aaag_status launch_cull(aaag_workspace* ws, cudaStream_t st) {
   unsigned long long* look_b = ws->cull_lookback + (ws->n_max + kOffTile - 1) / kOffTile + 1;
   const int64_t tiles_a = std::max<int64_t>((n + kOffTile - 1) / kOffTile, 1);
   const unsigned grid_a = (unsigned)std::min<int64_t>(tiles_a, (int64_t)lc.sms * lc.cull_a_per_sm);
-  chunk_offsets_kernel<<<grid_a, kThreads, 0, st>>>(ws->counts, n, ws->chunk_capacity, ws->offsets,
+  launch_chained(chunk_offsets_kernel, grid_a, kThreads, 0, st, ws->counts, n, ws->chunk_capacity, ws->offsets,
                                                     ws->chunk_owner, look_a, ws->stats, n_chunks, ws->sort_hist,
-                                                    ws->sort_counters);
+                                                    ws->sort_counters, ws->ranges, (int)ws->n_tiles);
   aaag_status e = check_launch("chunk_offsets");
   if (e != AAAG_OK) return e;
   const unsigned grid_t = (unsigned)std::max<int64_t>(
       std::min<int64_t>((ws->chunk_capacity + kWarps - 1) / kWarps, (int64_t)lc.sms * 16), 1);
-  cull_test_kernel<<<grid_t, kThreads, 0, st>>>(ws->records, ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets,
+  launch_chained(cull_test_kernel, grid_t, kThreads, 0, st, ws->records, ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets,
                                                 n_chunks, ws->chunk_capacity, ws->chunk_mask, ws->stats);
   e = check_launch("cull_test");
   if (e != AAAG_OK) return e;
   const int64_t tiles_b = std::max<int64_t>((ws->chunk_capacity + kChunkTile - 1) / kChunkTile, 1);
   const unsigned grid_b = (unsigned)std::min<int64_t>(tiles_b, (int64_t)lc.sms * lc.cull_b_per_sm);
-  cull_emit_kernel<<<grid_b, kThreads, 0, st>>>(ws->records, ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets, n_chunks,
+  launch_chained(cull_emit_kernel, grid_b, kThreads, 0, st, ws->records, ws->aux, ws->fc_dev, ws->chunk_owner, ws->offsets, n_chunks,
                                                 ws->chunk_capacity, ws->chunk_mask, ws->keys[0], ws->vals[0],
                                                 ws->capacity, look_b, ws->stats, n_pairs);
   return check_launch("cull_emit");

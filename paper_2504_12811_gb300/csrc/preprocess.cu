@@ -447,6 +447,7 @@ __device__ __forceinline__ bool preprocess_one(const SceneDev& s, const FrameCon
 __global__ void __launch_bounds__(256)
 preprocess_test_kernel(SceneDev s, const FrameConst* __restrict__ fcp, uint32_t* __restrict__ chunks,
                        uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand, int vec4) {
+  pdl_begin();
   const FrameConst fc = *fcp;
   const int lane = threadIdx.x & 31;
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
@@ -497,6 +498,7 @@ __global__ void __launch_bounds__(256, 2)
 preprocess_kernel(SceneDev s, const FrameConst* __restrict__ fcp, const uint32_t* __restrict__ cand,
                   const uint32_t* __restrict__ n_cand, Record* __restrict__ rec, uint4* __restrict__ aux,
                   uint32_t* __restrict__ chunks, unsigned long long* __restrict__ stats) {
+  pdl_begin();
   const FrameConst fc = *fcp;
   const uint32_t count = *n_cand;
   uint32_t nvis = 0;
@@ -530,12 +532,12 @@ aaag_status launch_preprocess(const SceneDev& s, aaag_workspace* ws, cudaStream_
   auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0u; };
   const int vec4 = a16(s.means) && a16(s.log_scales) && a16(s.opacity_logits) && a16(s.vhat_train) &&
                    a16(ws->counts);
-  preprocess_test_kernel<<<(unsigned)tblocks, threads, 0, st>>>(s, ws->fc_dev, ws->counts, ws->candidates, n_cand,
+  launch_chained(preprocess_test_kernel, (unsigned)tblocks, threads, 0, st, s, ws->fc_dev, ws->counts, ws->candidates, n_cand,
                                                                 vec4);
   aaag_status e = check_launch("preprocess_test");
   if (e != AAAG_OK) return e;
   const unsigned grid = (unsigned)std::min<int64_t>(blocks, pre_blocks);
-  preprocess_kernel<<<grid, threads, 0, st>>>(s, ws->fc_dev, ws->candidates, n_cand, ws->records, ws->aux,
+  launch_chained(preprocess_kernel, grid, threads, 0, st, s, ws->fc_dev, ws->candidates, n_cand, ws->records, ws->aux,
                                               ws->counts, ws->stats);
   return check_launch("preprocess");
 }

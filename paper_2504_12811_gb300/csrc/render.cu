@@ -77,7 +77,7 @@ __device__ __forceinline__ void render_tile(TileSmem<IndexQueue>& s, int tile, c
   bl.Cr = bl.Cg = bl.Cb = 0.0f;
   bl.done = !in_image;
   bl.nblend = 0;
-  unsigned long long neval = 0;
+  uint32_t neval = 0;   // evaluations of this pixel (far below 2^32 per tile)
   uint32_t nmis = 0, npass = 0;
   traverse_tile<false, EXACT>(s, ranges[tile], keys, vals, rec, aux, fc, tx, ty, (float)lx + 0.5f, (float)ly + 0.5f,
                               bl, neval, nmis, npass);
@@ -117,6 +117,7 @@ __device__ __forceinline__ void render_tile(TileSmem<IndexQueue>& s, int tile, c
 __global__ void __launch_bounds__(1024)
 tile_order_kernel(const uint2* __restrict__ ranges, const FrameConst* __restrict__ fcp,
                   uint32_t* __restrict__ order, uint32_t* __restrict__ counter) {
+  pdl_begin();
   constexpr int kBuckets = 64;
   __shared__ uint32_t base[kBuckets];
   const int n_tiles = fcp->tiles_x * fcp->tiles_y;
@@ -174,6 +175,7 @@ render_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ key
               const FrameConst* __restrict__ fcp, float* __restrict__ rgb, float* __restrict__ alpha,
               float* __restrict__ final_T, uint32_t* __restrict__ n_blended, unsigned long long* __restrict__ stats,
               const uint32_t* __restrict__ order, uint32_t* __restrict__ counter) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileSmem<IndexQueue>& s = *reinterpret_cast<TileSmem<IndexQueue>*>(smem_raw);
   __shared__ uint32_t s_item;
@@ -281,7 +283,7 @@ aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, fl
 }
 
 aaag_status launch_tile_order(aaag_workspace* ws, uint32_t* counter, cudaStream_t st) {
-  tile_order_kernel<<<1, 1024, 0, st>>>(ws->ranges, ws->fc_dev, ws->tile_order, counter);
+  launch_chained(tile_order_kernel, 1, 1024, 0, st, ws->ranges, ws->fc_dev, ws->tile_order, counter);
   return check_launch("tile_order");
 }
 
@@ -293,7 +295,7 @@ aaag_status launch_render(aaag_workspace* ws, float* rgb, float* alpha, cudaStre
   if (e != AAAG_OK) return e;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)lc.sms * lc.serve_per_sm, ws->n_tiles));
   auto kernel = (ws->fc.flags & (AAAG_FLAG_NO_RESORT | AAAG_FLAG_KBUFFER)) ? render_kernel<false> : render_kernel<true>;
-  kernel<<<grid, kTilePixels, kForwardSmemBytes, st>>>(ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->aux,
+  launch_chained(kernel, grid, kTilePixels, kForwardSmemBytes, st, ws->ranges, ws->keys[alt], ws->vals[alt], ws->records, ws->aux,
                                                         ws->fc_dev, rgb, alpha, ws->final_T, ws->n_blended, ws->stats,
                                                         ws->tile_order, counter);
   return check_launch("render");

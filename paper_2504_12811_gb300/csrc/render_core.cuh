@@ -325,7 +325,7 @@ __device__ __forceinline__ void traverse_tile(TileSmem<typename Blender::Queue>&
                                               const uint32_t* __restrict__ vals, const Record* __restrict__ rec,
                                               const uint4* __restrict__ aux, const FrameConst& fc, int tile_x,
                                               int tile_y, float x, float y, Blender& bl,
-                                              unsigned long long& neval, uint32_t& nmis, uint32_t& npass) {
+                                              uint32_t& neval, uint32_t& nmis, uint32_t& npass) {
   const int ox = tile_x * kTile, oy = tile_y * kTile;
   const float cxm = fc.cx - (float)ox, cym = fc.cy - (float)oy;
   const uint32_t wbit = 1u << (threadIdx.x >> 5);

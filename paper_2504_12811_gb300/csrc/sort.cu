@@ -40,6 +40,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 __global__ void sort_init_kernel(uint32_t* hist, uint32_t* counters, unsigned long long* epoch) {
+  pdl_begin();
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) hist[i] = 0;
   if (threadIdx.x < 4) counters[threadIdx.x] = 0;
   if (threadIdx.x == 0) *epoch += 1ull;
@@ -50,6 +51,7 @@ sort_histogram_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restr
                       int64_t n_max, int passes, uint32_t* __restrict__ hist,
                       unsigned long long* __restrict__ lookback, int64_t lb_words,
                       const unsigned long long* __restrict__ epoch) {
+  pdl_begin();
   __shared__ uint32_t sh[4][kRadix];
   // a new cycle of look-back tags: clear every word (the passes come later)
   if ((*epoch & ((1ull << 29) - 1ull)) == 0ull)
@@ -276,6 +278,7 @@ sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
                  unsigned long long* __restrict__ lookback,
                  const unsigned long long* __restrict__ epoch_dev,
                  unsigned long long* __restrict__ timeout_flag) {
+  pdl_begin();
   __shared__ SortSmem<(WIDE ? kWideItems : kSortItems) * kSortThreads> sm;
   const int64_t n = min((int64_t)*n_dev, n_max);
   const unsigned long long epoch = ((*epoch_dev) * 8ull + (unsigned long long)pass) & 0xffffffffull;
@@ -297,6 +300,7 @@ sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev,
                               int64_t n_max, int depth_bits, uint2* __restrict__ ranges) {
+  pdl_begin();
   const int64_t n = min((int64_t)*n_dev, n_max);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -336,9 +340,9 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
     return AAAG_OK;
   }
   const LaunchConfig& lc = launch_config();
-  if (!prepared) sort_init_kernel<<<1, 256, 0, st>>>(hist, counters, epoch);
+  if (!prepared) launch_chained(sort_init_kernel, 1, 256, 0, st, hist, counters, epoch);
   const int64_t hblocks = std::min<int64_t>((n_max + 4095) / 4096, (int64_t)lc.sms * 4);
-  sort_histogram_kernel<<<(unsigned)hblocks, 256, 0, st>>>(keys, n_dev, n_max, passes, hist, lookback,
+  launch_chained(sort_histogram_kernel, (unsigned)hblocks, 256, 0, st, keys, n_dev, n_max, passes, hist, lookback,
                                                            lookback_words, epoch);
   aaag_status e = check_launch("sort_histogram");
   if (e != AAAG_OK) return e;
@@ -354,7 +358,7 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
   uint32_t* kout = keys_alt;
   uint32_t* vout = vals_alt;
   for (int p = 0; p < passes; ++p) {
-    pass_kernel<<<(unsigned)grid, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_dev, n_max, p, hist,
+    launch_chained(pass_kernel, (unsigned)grid, kSortThreads, 0, st, kin, vin, kout, vout, n_dev, n_max, p, hist,
                                                                counters + p, lookback, epoch, timeout_flag);
     e = check_launch("sort_pass");
     if (e != AAAG_OK) return e;
@@ -381,11 +385,10 @@ aaag_status launch_sort_pairs(aaag_workspace* ws, cudaStream_t st) {
                           (ws->n_sort_tiles + 1) * kRadix, ws->stats + kStatSortEpoch, ws->stats + kStatTimeout, &alt, st, true);
   if (e != AAAG_OK) return e;
   ws->sorted_in_alt = alt;
-  if (cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * (size_t)ws->n_tiles, st) != cudaSuccess)
-    return check_launch("ranges memset");
+  // (the tile ranges were zeroed by K2's chunk_offsets_kernel)
   const int64_t rblocks = std::min<int64_t>((ws->capacity + 255) / 256, (int64_t)launch_config().sms * 8);
-  ranges_kernel<<<(unsigned)std::max<int64_t>(rblocks, 1), 256, 0, st>>>(
-      ws->keys[alt], n_dev, ws->capacity, ws->fc.depth_bits, ws->ranges);
+  launch_chained(ranges_kernel, (unsigned)std::max<int64_t>(rblocks, 1), 256, 0, st,
+                 ws->keys[alt], n_dev, ws->capacity, ws->fc.depth_bits, ws->ranges);
   return check_launch("ranges");
 }
 
