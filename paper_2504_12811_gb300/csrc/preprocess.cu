@@ -474,7 +474,12 @@ preprocess_test_kernel(SceneDev s, const FrameConst* __restrict__ fcp, uint32_t*
       }
     }
   }
-  // append the survivors: warp scan of the per-thread counts
+  // append the survivors: scan of the per-thread counts over the block and
+  // one atomic per block (one per warp serialised on the single counter:
+  // 125k of them at 16M Gaussians)
+  __shared__ uint32_t s_warp[8];
+  __shared__ uint32_t s_base;
+  const int warp = threadIdx.x >> 5;
   const uint32_t c = (uint32_t)__popc(pass);
   uint32_t incl = c;
 #pragma unroll
@@ -482,10 +487,19 @@ preprocess_test_kernel(SceneDev s, const FrameConst* __restrict__ fcp, uint32_t*
     const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += y;
   }
-  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-  uint32_t at = 0u;
-  if (lane == 0 && total) at = atomicAdd(n_cand, total);
-  at = __shfl_sync(0xffffffffu, at, 0) + incl - c;
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t sum = 0u;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      const uint32_t t = s_warp[w];
+      s_warp[w] = sum;
+      sum += t;
+    }
+    s_base = sum ? atomicAdd(n_cand, sum) : 0u;
+  }
+  __syncthreads();
+  uint32_t at = s_base + s_warp[warp] + incl - c;
   for (int j = 0; j < 4; ++j)
     if (pass >> j & 1u) cand[at++] = (uint32_t)(i0 + j);
 }
