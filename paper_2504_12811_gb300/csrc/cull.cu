@@ -35,7 +35,8 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kOffItems = 8;                        // Gaussians per thread in kernel A
 constexpr int kOffTile = kThreads * kOffItems;      // 2048
-constexpr int kChunkTile = kWarps * 32;             // 256 chunks per tile of kernel B
+constexpr int kChunkTile = kWarps * 32;             // 256 chunks per tile of kernel C
+constexpr int kTestWindow = 16;                     // chunks per warp window of kernel B
 
 constexpr unsigned long long kLbAggregate = 1ull << 38;
 constexpr unsigned long long kLbInclusive = 2ull << 38;
@@ -279,27 +280,69 @@ cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   const bool cull = !(fc.flags & AAAG_FLAG_NO_CULL);
   unsigned long long tested = 0;
-  for (int64_t c = warp0; c < nch; c += nwarps) {
-    const uint32_t g = owner[c];
-    const uint4 a = aux[g];
-    const int local = (int)(c - (int64_t)chunk_offsets[g]);
-    int tx0, ty0, tx1, ty1;
-    unpack_rect(a, tx0, ty0, tx1, ty1);
-    const int nx = tx1 - tx0 + 1, total = nx * (ty1 - ty0 + 1);
-    const int j = local * 32 + lane;
-    bool keep = false;
-    if (j < total) {
-      if (cull) {
-        const float4* r = reinterpret_cast<const float4*>(rec + g);
-        keep = tile_needed(__ldg(r + 0), __ldg(r + 1), __ldg(r + 2), __uint_as_float(a.z), fc, tx0 + j % nx,
-                           ty0 + j / nx);
-      } else {
-        keep = true;
-      }
-      ++tested;
+  // A warp takes a window of kTestWindow consecutive chunks (lane i < kTestWindow
+  // holds chunk w0 + i) and tests their tiles in rounds: each round packs as
+  // many of the next chunks as fit in 32 lanes, one lane per tile, so the
+  // chunks of small Gaussians (a few tiles each) share a round instead of
+  // leaving most lanes idle.
+  for (int64_t w0 = warp0 * kTestWindow; w0 < nch; w0 += nwarps * kTestWindow) {
+    const int64_t c = w0 + lane;
+    const bool valid = lane < kTestWindow && c < nch;
+    uint32_t g = 0u, cnt = 0u;
+    uint4 a = make_uint4(0u, 0u, 0u, 0u);
+    int local = 0;
+    if (valid) {
+      g = owner[c];
+      a = aux[g];
+      local = (int)(c - (int64_t)chunk_offsets[g]);
+      int tx0, ty0, tx1, ty1;
+      unpack_rect(a, tx0, ty0, tx1, ty1);
+      const int total = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+      cnt = (uint32_t)min(32, total - 32 * local);
     }
-    const unsigned ball = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) masks[c] = ball;
+    uint32_t mine = 0u;   // the mask of this lane's chunk
+    int next = 0;         // first chunk of the window not yet tested (warp-uniform)
+    while (__any_sync(0xffffffffu, valid && lane >= next)) {
+      // inclusive scan of the tile counts of the untested chunks
+      const uint32_t v = (valid && lane >= next) ? cnt : 0u;
+      uint32_t incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t excl = incl - v;
+      const bool in_round = v > 0u && incl <= 32u;   // always true for the chunk `next`
+      const unsigned starts = __reduce_or_sync(0xffffffffu, in_round ? 1u << excl : 0u);
+      const int n_round = __popc(__ballot_sync(0xffffffffu, in_round));
+      const uint32_t used = __reduce_max_sync(0xffffffffu, in_round ? incl : 0u);
+      // this lane's tile: chunk `slot` of the window, tile t of that chunk
+      const int slot = next + __popc(starts & ((2u << lane) - 1u)) - 1;
+      const uint32_t gs = __shfl_sync(0xffffffffu, g, slot);
+      const uint32_t ax = __shfl_sync(0xffffffffu, a.x, slot), ay = __shfl_sync(0xffffffffu, a.y, slot);
+      const uint32_t az = __shfl_sync(0xffffffffu, a.z, slot);
+      const int ls = __shfl_sync(0xffffffffu, local, slot);
+      const uint32_t es = __shfl_sync(0xffffffffu, excl, slot);
+      bool keep = false;
+      if ((uint32_t)lane < used) {
+        int tx0, ty0, tx1, ty1;
+        unpack_rect(make_uint4(ax, ay, 0u, 0u), tx0, ty0, tx1, ty1);
+        const int nx = tx1 - tx0 + 1;
+        const int j = ls * 32 + (lane - (int)es);
+        if (cull) {
+          const float4* r = reinterpret_cast<const float4*>(rec + gs);
+          keep = tile_needed(__ldg(r + 0), __ldg(r + 1), __ldg(r + 2), __uint_as_float(az), fc, tx0 + j % nx,
+                             ty0 + j / nx);
+        } else {
+          keep = true;
+        }
+        ++tested;
+      }
+      const unsigned ball = __ballot_sync(0xffffffffu, keep);
+      if (in_round) mine = (ball >> excl) & (cnt == 32u ? 0xffffffffu : ((1u << cnt) - 1u));
+      next += n_round;
+    }
+    if (valid) masks[c] = mine;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tested += __shfl_xor_sync(0xffffffffu, tested, o);
