@@ -228,9 +228,12 @@ aaag_status aaag_preprocess(const aaag_scene* scene /* host struct */,
  * with the ray's maximum at t* >= znear (the per-pixel near-plane rule over
  * the tile's area).  Emits one (key, Gaussian index) pair per kept tile,
  * key = tile id (high bits) and the quantised depth bound (low bits; the
- * layout is in aaag_workspace_view).  Pairs beyond the capacity are dropped
- * and flagged (aaag_get_stats -> capacity_overflow); a look-back wait that
- * gives up sets the timeout flag.
+ * layout is in aaag_workspace_view): the larger of the Gaussian's own lower
+ * bound of t* and the smallest t* over the tile's pixel centres (attained
+ * at a corner), lowered by a rounding allowance and rounded down.  Also
+ * empties the tile ranges that aaag_sort fills.  Pairs beyond the capacity
+ * are dropped and flagged (aaag_get_stats -> capacity_overflow); a
+ * look-back wait that gives up sets the timeout flag.
  * Errors: INVALID_ARG, CUDA.
  * ------------------------------------------------------------------------ */
 aaag_status aaag_cull(aaag_workspace* ws, cudaStream_t stream);
