@@ -293,13 +293,27 @@ __device__ __forceinline__ Basic basic_early(const float* m, const float* l, flo
 // 2 ln(255 o) >= tau because the amplitude factor of Eq. 12 is at most 1.  A
 // sphere wholly outside one side plane of the image frustum or in front of
 // z_near holds no visible point.
-__device__ __forceinline__ bool may_be_visible(const Basic& b, const FrameConst& fc) {
-  const float amin = kAlphaMin * (1.0f - 1e-5f);
-  // the EWA splat of the 2D-evaluation ablation is not bounded by the sphere
-  if (fc.flags & AAAG_FLAG_EVAL_2D) return b.vz >= fc.znear && b.opac > amin;
+// The same test with the fast logarithm and the lowered opacity threshold,
+// for the inputs of basic_early (the vectorised path).  (Kept apart from the
+// exact one: with a single function for both paths the vectorised loop
+// compiled to code 15% slower at 16M Gaussians.)
+__device__ __forceinline__ bool may_be_visible_fast(const Basic& b, const FrameConst& fc) {
+  if (fc.flags & AAAG_FLAG_EVAL_2D) return b.vz >= fc.znear && b.opac > kAlphaMin * (1.0f - 1e-5f);
   const float tau_max = 2.0f * __logf(fmaxf(b.opac * 255.0f, 1.0f));
   const float rad = fmaf(sqrtf(inflate_tau(tau_max) * fmaxf(b.hx, fmaxf(b.hy, b.hz))), 1.001f, 1e-6f);
-  bool near_view = b.vz + rad >= fc.znear && b.opac > amin;
+  bool near_view = b.vz + rad >= fc.znear && b.opac > kAlphaMin * (1.0f - 1e-5f);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    near_view &= fmaf(fc.side[j][0], b.vx, fmaf(fc.side[j][1], b.vy, fc.side[j][2] * b.vz)) >= -rad;
+  return near_view;
+}
+
+__device__ __forceinline__ bool may_be_visible(const Basic& b, const FrameConst& fc) {
+  // the EWA splat of the 2D-evaluation ablation is not bounded by the sphere
+  if (fc.flags & AAAG_FLAG_EVAL_2D) return b.vz >= fc.znear && b.opac > kAlphaMin;
+  const float tau_max = 2.0f * logf(fmaxf(b.opac * 255.0f, 1.0f));
+  const float rad = fmaf(sqrtf(inflate_tau(tau_max) * fmaxf(b.hx, fmaxf(b.hy, b.hz))), 1.001f, 1e-6f);
+  bool near_view = b.vz + rad >= fc.znear && b.opac > kAlphaMin;
 #pragma unroll
   for (int j = 0; j < 4; ++j)
     near_view &= fmaf(fc.side[j][0], b.vx, fmaf(fc.side[j][1], b.vy, fc.side[j][2] * b.vz)) >= -rad;
@@ -491,7 +505,7 @@ preprocess_test_kernel(SceneDev s, const FrameConst* __restrict__ fcp, uint32_t*
     const float oo[4] = {op.x, op.y, op.z, op.w}, vv[4] = {vt.x, vt.y, vt.z, vt.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (may_be_visible(basic_early(mm + 3 * j, ll + 3 * j, oo[j], vv[j], fc), fc)) pass |= 1u << j;
+      if (may_be_visible_fast(basic_early(mm + 3 * j, ll + 3 * j, oo[j], vv[j], fc), fc)) pass |= 1u << j;
     *reinterpret_cast<uint4*>(chunks + i0) = make_uint4(0u, 0u, 0u, 0u);
   } else {
     for (int j = 0; j < 4; ++j) {
