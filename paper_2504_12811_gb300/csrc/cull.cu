@@ -10,11 +10,12 @@
 //      per-Gaussian chunk counts (written by K1) -> each Gaussian's first
 //      chunk, and each Gaussian writes its index into its chunks' owner slots
 //      (it also prepares K3's counters and empties K4's tile ranges).
-//   B. cull_test_kernel: one warp per chunk (grid-stride), one lane per tile;
-//      the ballot of the needed tiles is stored per chunk.
+//   B. cull_test_kernel: windows of 16 chunks per warp (grid-stride), one
+//      lane per tile, several small chunks packed into one round of 32 lanes;
+//      the mask of the needed tiles is stored per chunk.
 //   C. cull_emit_kernel: tiles of 256 chunks; the tile's pair count is
-//      resolved into its global pair offset by look-back, and its warps write
-//      the pairs.
+//      resolved into its global pair offset by look-back, and each lane
+//      writes its own chunk's pairs.
 // Pairs therefore land at deterministic positions: Gaussian order, then
 // rectangle row-major tile order.  Chunk and pair counts stay on the device.
 //
@@ -265,8 +266,8 @@ __device__ __forceinline__ uint32_t tile_depth_key(const KeyGeom& kg, const Fram
   return min((__float_as_uint(z) - fc.znear_bits) >> fc.depth_shift, dmax);
 }
 
-// One warp per chunk (grid-stride), one lane per tile: the warp ballot of the
-// chunk's needed tiles is stored.
+// Windows of kTestWindow chunks per warp (grid-stride), one lane per tile: the
+// mask of each chunk's needed tiles is stored.
 __global__ void __launch_bounds__(kThreads, 3)
 cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
                  const uint32_t* __restrict__ owner, const uint32_t* __restrict__ chunk_offsets,
@@ -350,8 +351,8 @@ cull_test_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, 
 }
 
 // Tiles of 256 chunks (8 warps x 32): the tile's pair count is resolved into
-// its global pair offset by look-back, then each warp writes the pairs of its
-// 32 chunks in chunk order (lane i first loads the geometry of chunk i).
+// its global pair offset by look-back, then lane i of each warp writes the
+// pairs of the warp's chunk i at their scanned positions.
 __global__ void __launch_bounds__(kThreads)
 cull_emit_kernel(const Record* __restrict__ rec, const uint4* __restrict__ aux, const FrameConst* __restrict__ fcp,
                  const uint32_t* __restrict__ owner, const uint32_t* __restrict__ chunk_offsets,
