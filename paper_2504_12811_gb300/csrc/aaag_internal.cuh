@@ -203,6 +203,7 @@ struct LaunchConfig {
   int cull_b_per_sm;     // cull_emit_kernel
   int sort_pass_per_sm;  // sort_pass_kernel
   int sort_wide_per_sm;  // sort_pass_kernel, 12 keys per thread
+  int sort_xwide_per_sm; // sort_pass_kernel_x16, 16 keys per thread
   int serve_per_sm;      // serve_render_kernel
   int backward_per_sm;   // render_backward_kernel
 };

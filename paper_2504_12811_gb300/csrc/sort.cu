@@ -3,10 +3,10 @@
 // minor).
 //
 // Onesweep structure: one histogram kernel reads every key once and counts
-// all digit positions; then one kernel per 8-bit digit ranks a 1024-, 2048- or 3072-key tile
-// per block (warp-level multisplit with __match_any_sync, preserving input
-// order), publishes its per-digit counts, resolves the exclusive prefix of
-// earlier tiles by decoupled look-back, and scatters through shared memory.
+// all digit positions; then one kernel per 8-bit digit ranks a 1024- to 4096-key
+// tile per block (warp-level multisplit with __match_any_sync, preserving
+// input order), publishes its per-digit counts, resolves the exclusive prefix
+// of earlier tiles by decoupled look-back, and scatters through shared memory.
 // Tiles are taken in launch order from an atomic counter, so every tile a
 // block waits on belongs to a block that is already running.
 //
@@ -169,8 +169,10 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem<TILE>& sm, const uint32
     const int64_t tile = s_tile;
     if (tile >= n_tiles) break;
 
-    // ---- load (warp-striped: coalesced) and rank within each warp
-    uint32_t k[ITEMS], v[ITEMS], r[ITEMS];
+    // ---- load the keys (warp-striped: coalesced) and rank within each warp;
+    // the values are read only at the scatter, so that they hold no
+    // registers while the keys are ranked
+    uint32_t k[ITEMS], r[ITEMS];
     const uint32_t n32 = (uint32_t)n;
     const uint32_t base = (uint32_t)tile * kTileKeys + (uint32_t)warp * (32 * ITEMS) + (uint32_t)lane;
 #pragma unroll
@@ -178,7 +180,6 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem<TILE>& sm, const uint32
       const uint32_t idx = base + j * 32;
       const bool ok = idx < n32;
       k[j] = ok ? keys_in[idx] : 0xffffffffu;
-      v[j] = ok ? vals_in[idx] : 0u;
     }
     for (int i = lane; i < kRadix; i += 32) s_warp[warp][i] = 0;
     __syncwarp();
@@ -221,8 +222,9 @@ __device__ __forceinline__ void sort_pass_tiles(SortSmem<TILE>& sm, const uint32
     for (int j = 0; j < ITEMS; ++j) {
       const uint32_t d = (k[j] >> shift) & 0xffu;
       const uint32_t pos = s_digit_start[d] + s_warp[warp][d] + r[j];
+      const uint32_t idx = base + j * 32;
       s_keys[pos] = k[j];
-      s_vals[pos] = v[j];
+      s_vals[pos] = idx < n32 ? vals_in[idx] : 0u;
     }
 
     uint32_t prefix = 0;
@@ -263,31 +265,34 @@ __device__ __forceinline__ int sort_items_for(int64_t n) {
   return n >= kSortWideKeys / 2 ? 8 : 4;
 }
 
-// WIDE: tiles of 12 keys per thread (3072), for sorts of at least
-// kSortWideMin keys whose size is known on the host; its 77 registers leave
-// three blocks per SM, so it is a kernel of its own (the other keeps four).
+// Sorts whose size is known on the host take larger tiles: 12 keys per
+// thread (3072) from kSortWideMin keys, 16 (4096) from kSortXWideMin.  Each
+// size is a kernel of its own, so that each gets its own register budget
+// (the 16-key one capped for three blocks per SM).
 constexpr int kWideItems = 12;
+constexpr int kXWideItems = 16;
 constexpr int64_t kSortWideMin = 4 << 20;
+constexpr int64_t kSortXWideMin = 32 << 20;
 
-template <bool WIDE>
-__global__ void __launch_bounds__(kSortThreads)
-sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                 const uint32_t* __restrict__ n_dev, int64_t n_max, int pass,
-                 const uint32_t* __restrict__ hist, uint32_t* __restrict__ counter,
-                 unsigned long long* __restrict__ lookback,
-                 const unsigned long long* __restrict__ epoch_dev,
-                 unsigned long long* __restrict__ timeout_flag) {
+// One pass; ITEMS = 0 picks 4 or 8 keys per thread from the device count.
+template <int ITEMS>
+__device__ __forceinline__ void sort_pass(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                                          uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                                          const uint32_t* __restrict__ n_dev, int64_t n_max, int pass,
+                                          const uint32_t* __restrict__ hist, uint32_t* __restrict__ counter,
+                                          unsigned long long* __restrict__ lookback,
+                                          const unsigned long long* __restrict__ epoch_dev,
+                                          unsigned long long* __restrict__ timeout_flag) {
   pdl_begin();
-  __shared__ SortSmem<(WIDE ? kWideItems : kSortItems) * kSortThreads> sm;
+  __shared__ SortSmem<(ITEMS ? ITEMS : kSortItems) * kSortThreads> sm;
   const int64_t n = min((int64_t)*n_dev, n_max);
   const unsigned long long epoch = ((*epoch_dev) * 8ull + (unsigned long long)pass) & 0xffffffffull;
   const unsigned long long tag = epoch << 32;
   // global exclusive offset of digit `threadIdx.x` for this pass
   const uint32_t gofs = block_exclusive_scan_256(hist[pass * kRadix + threadIdx.x], sm.tmp);
-  if constexpr (WIDE) {
-    sort_pass_tiles<kWideItems>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback,
-                                tag, timeout_flag);
+  if constexpr (ITEMS != 0) {
+    sort_pass_tiles<ITEMS>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
+                           timeout_flag);
   } else {
     if (sort_items_for(n) == 8)
       sort_pass_tiles<8>(sm, keys_in, vals_in, keys_out, vals_out, n, 8 * pass, gofs, counter, lookback, tag,
@@ -297,6 +302,24 @@ sort_pass_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
                          timeout_flag);
   }
 }
+
+#define AAAG_SORT_PASS_ARGS                                                                              \
+  const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out, \
+      uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ n_dev, int64_t n_max, int pass,          \
+      const uint32_t *__restrict__ hist, uint32_t *__restrict__ counter, unsigned long long *__restrict__ lookback, \
+      const unsigned long long *__restrict__ epoch_dev, unsigned long long *__restrict__ timeout_flag
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(AAAG_SORT_PASS_ARGS) {
+  sort_pass<WIDE ? kWideItems : 0>(keys_in, vals_in, keys_out, vals_out, n_dev, n_max, pass, hist, counter, lookback,
+                                   epoch_dev, timeout_flag);
+}
+
+__global__ void __launch_bounds__(kSortThreads, 3) sort_pass_kernel_x16(AAAG_SORT_PASS_ARGS) {
+  sort_pass<kXWideItems>(keys_in, vals_in, keys_out, vals_out, n_dev, n_max, pass, hist, counter, lookback, epoch_dev,
+                         timeout_flag);
+}
+#undef AAAG_SORT_PASS_ARGS
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_dev,
                               int64_t n_max, int depth_bits, uint2* __restrict__ ranges) {
@@ -319,6 +342,9 @@ void configure_sort(LaunchConfig& c) {
   per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_pass_kernel<true>, kSortThreads, 0);
   c.sort_wide_per_sm = std::max(1, per_sm);
+  per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_pass_kernel_x16, kSortThreads, 0);
+  c.sort_xwide_per_sm = std::max(1, per_sm);
 }
 
 size_t radix_sort_scratch(int64_t n_max) {
@@ -346,13 +372,17 @@ aaag_status radix_sort_device_n(uint32_t* keys, uint32_t* vals, uint32_t* keys_a
                                                            lookback_words, epoch);
   aaag_status e = check_launch("sort_histogram");
   if (e != AAAG_OK) return e;
-  // wide tiles when the count is known to be large (n_max is the count
+  // wider tiles when the count is known to be large (n_max is the count
   // itself, not a capacity)
-  const bool wide = n_exact && n_max >= kSortWideMin;
-  const int64_t tiles = wide ? (n_max + kWideItems * kSortThreads - 1) / (kWideItems * kSortThreads)
-                             : sort_max_tiles(n_max);
-  const int64_t grid = std::min<int64_t>(tiles, (int64_t)lc.sms * (wide ? lc.sort_wide_per_sm : lc.sort_pass_per_sm));
-  auto pass_kernel = wide ? sort_pass_kernel<true> : sort_pass_kernel<false>;
+  const int items = !n_exact ? 0 : n_max >= kSortXWideMin ? kXWideItems : n_max >= kSortWideMin ? kWideItems : 0;
+  const int64_t tiles = items ? (n_max + items * kSortThreads - 1) / (items * kSortThreads) : sort_max_tiles(n_max);
+  const int per_sm = items == kXWideItems ? lc.sort_xwide_per_sm
+                     : items == kWideItems ? lc.sort_wide_per_sm
+                                           : lc.sort_pass_per_sm;
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)lc.sms * per_sm);
+  auto pass_kernel = items == kXWideItems ? sort_pass_kernel_x16
+                     : items == kWideItems ? sort_pass_kernel<true>
+                                           : sort_pass_kernel<false>;
   uint32_t* kin = keys;
   uint32_t* vin = vals;
   uint32_t* kout = keys_alt;

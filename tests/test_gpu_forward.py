@@ -297,10 +297,11 @@ def test_sort_is_bit_exact(wl, ci):
             assert ranges[tile, 0] == ranges[tile, 1]
 
 
-# sizes of at least 4M keys take the wide-tile kernel (3072 keys per tile)
+# sizes of at least 4M keys take the 3072-key tiles, of at least 32M the 4096-key tiles
 @pytest.mark.parametrize("n,key_bits", [(1, 32), (17, 8), (4095, 13), (4096, 32), (4097, 24),
                                         (100_003, 32), (1 << 20, 20), ((1 << 21) + 77, 32),
-                                        (4 << 20, 24), ((4 << 20) + 3071, 32), ((9 << 20) + 5, 32)])
+                                        (4 << 20, 24), ((4 << 20) + 3071, 32), ((9 << 20) + 5, 32),
+                                        (32 << 20, 24), ((32 << 20) + 4093, 32)])
 def test_radix_sort_entry_point(n, key_bits):
     rng = np.random.default_rng(n + key_bits)
     keys = rng.integers(0, 1 << key_bits, n, dtype=np.uint64).astype(np.uint32)
