@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--sort-keys", type=int, default=0,
                     help="only time aaag_radix_sort on this many random keys with values and exit")
     ap.add_argument("--sort-bits", type=int, default=32)
+    ap.add_argument("--pre-gaussians", type=int, default=0,
+                    help="only time aaag_preprocess of an N-Gaussian synthetic scene (the hbm.large scene)")
     ap.add_argument("--sort-reps", type=int, default=5)
     return ap.parse_args()
 
@@ -188,13 +190,12 @@ def run_serving(args, dev):
     return out
 
 
-def run_hbm_large(dev, flush, hbm_peak, n=16_000_000, n_keys=64 << 20):
-    """Preprocess and sort at sizes where bandwidth, not launch latency, can
-    bound them: preprocess of a 16M-Gaussian synthetic scene generated on the
+def run_hbm_preprocess(dev, flush, n, reps=5):
+    """aaag_preprocess of an n-Gaussian synthetic scene generated on the
     device (means uniform in a 20 m box, log-scales N(-4, 1), opacity logits
-    N(0, 2), SH 3), seen from inside at 1920x1080, and a radix sort of 64M
-    random 32-bit keys with values, both through the C-ABI; bytes counted as
-    in the headline's `hbm` entry."""
+    N(0, 2), SH 3), seen from inside at 1920x1080: mean ms of `reps` calls
+    after one warm-up (L2 flushed before each), bytes per second counted as in
+    the headline's `hbm` entry, visible count."""
     import numpy as np
     import torch
     from paper_2504_12811_gb300 import aaag, scenes
@@ -216,7 +217,7 @@ def run_hbm_large(dev, flush, hbm_peak, n=16_000_000, n_keys=64 << 20):
     prm = aaag.make_params()
     sc = ds.struct()
     ms = []
-    for rep in range(6):
+    for rep in range(reps + 1):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -225,11 +226,26 @@ def run_hbm_large(dev, flush, hbm_peak, n=16_000_000, n_keys=64 << 20):
         torch.cuda.synchronize()
         if rep:
             ms.append(e0.elapsed_time(e1))
-    vis = aaag.stats(ws, check=False)["n_visible"]
+    vis = int(aaag.stats(ws, check=False)["n_visible"])
     pre_ms = float(np.mean(ms))
     pre_gbs = (n * 36 + vis * (16 + 192 + 64 + 16 + 4)) / (pre_ms / 1e3) / 1e9
     del ws, ds
     torch.cuda.empty_cache()
+    return pre_ms, pre_gbs, vis
+
+
+def run_hbm_large(dev, flush, hbm_peak, n=16_000_000, n_keys=64 << 20):
+    """Preprocess and sort at sizes where bandwidth, not launch latency, can
+    bound them: preprocess of a 16M-Gaussian synthetic scene (run_hbm_preprocess)
+    and a radix sort of 64M random 32-bit keys with values, both through the
+    C-ABI; bytes counted as in the headline's `hbm` entry."""
+    import numpy as np
+    import torch
+    from paper_2504_12811_gb300 import aaag
+    pre_ms, pre_gbs, vis = run_hbm_preprocess(dev, flush, n)
+    g = torch.Generator(device=dev)
+    g.manual_seed(22)
+    st = aaag.current_stream()
     keys = torch.randint(0, 2**31 - 1, (n_keys,), device=dev, dtype=torch.int64, generator=g).to(torch.int32)
     vals = torch.arange(n_keys, device=dev, dtype=torch.int32)
     k0, v0 = keys.clone(), vals.clone()
@@ -838,6 +854,14 @@ def main():
         print(json.dumps({"serving": run_serving(args, torch.device("cuda", 0))}), flush=True)
     elif args.sort_keys:
         run_sort_only(args)
+    elif args.pre_gaussians:
+        import torch
+        from paper_2504_12811_gb300 import build as B
+        B.build()
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        pre_ms, pre_gbs, vis = run_hbm_preprocess(dev, flush, args.pre_gaussians)
+        print(json.dumps({"gaussians": args.pre_gaussians, "visible": vis, "ms": pre_ms, "gbs": pre_gbs}))
     elif args.impl == "reference":
         run_reference(args)
     else:

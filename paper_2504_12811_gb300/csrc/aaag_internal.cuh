@@ -83,7 +83,8 @@ enum StatSlot : int {
   kStatMisorders = 5,
   kStatOverflow = 6,
   kStatTimeout = 7,
-  kStatCandidates = 8,     // uint32: Gaussians that passed the early preprocessing test
+  kStatCandidates = 8,     // uint32: Gaussians that passed the early preprocessing test (work
+                           // items taken, in the fused preprocessing of a large scene)
   kStatCullTileA = 9,      // uint32 tile counters of the cull's look-back kernels
   kStatCullTileB = 10,
   kStatChunks = 11,        // chunks of 32 candidate tiles (K2 work items)
@@ -199,6 +200,7 @@ aaag_status launch_render_batch(aaag_workspace* const* ws, float* const* rgb, fl
 struct LaunchConfig {
   int sms;
   int pre_per_sm;        // preprocess_kernel blocks per SM
+  int pre_fused_per_sm;  // preprocess_fused_kernel
   int cull_a_per_sm;     // chunk_offsets_kernel
   int cull_b_per_sm;     // cull_emit_kernel
   int sort_pass_per_sm;  // sort_pass_kernel

@@ -162,6 +162,60 @@ def test_preprocess_matches_oracle(wl, ci):
     assert st["n_visible"] == int(vis.sum())
 
 
+# Scenes of at least 4M Gaussians take the fused preprocessing kernel (test
+# and full work in one launch, survivors staged in a shared-memory ring).  The
+# work of one Gaussian depends on no other, so the oracle checks a sample: the
+# visible and culled Gaussians drawn at random, plus the ragged tail that the
+# scalar path handles.  Cameras: the whole cube in view (dense survivors) and
+# one inside it (sparse survivors, many straddling the near plane).
+LARGE_N = (8 << 20) + 1027
+
+
+@pytest.fixture(scope="module")
+def large_cube():
+    return scenes.uniform_cube_scene(LARGE_N, seed=5, sh_degree=3)
+
+
+@pytest.mark.parametrize("pos,target", [((0.4, -0.3, -3.2), (0.0, 0.0, 0.0)),
+                                        ((0.1, 0.2, 0.3), (0.6, -0.4, 1.5))])
+def test_preprocess_large_scene_sampled(large_cube, pos, target):
+    scene = large_cube
+    cam = scenes.make_camera(pos, target=target, width=256, height=160, fov_x_deg=50.0)
+    ws, _, _, _ = run_frame(scene, cam, capacity=1 << 20, stages=("pre",))
+    rec, aux, vis = gpu_records(ws, scene.n)
+    assert stats(ws)["n_visible"] == int(vis.sum())
+    rng = np.random.default_rng(17)
+    vis_idx, cull_idx = np.nonzero(vis)[0], np.nonzero(~vis)[0]
+    assert vis_idx.size > 1000 and cull_idx.size > 1000
+    sub = np.unique(np.concatenate([rng.choice(vis_idx, 700, replace=False),
+                                    rng.choice(cull_idx, 300, replace=False),
+                                    np.arange(scene.n - 7, scene.n)]))
+    rec, aux, vis = rec[sub], aux[sub], vis[sub]
+    prep = O.prepare(scene.subset(sub), cam)
+    alive = prep["alive"].numpy()
+    uu = (prep["u_cam"] ** 2).sum(-1).numpy()
+    tau = prep["tau"].numpy()
+    oh = prep["o_hat"].numpy()
+    edge = (np.abs(uu - tau) < 1e-3 * np.abs(tau)) | (np.abs(oh * 255 - 1) < 1e-3)
+    assert not np.any(vis & ~alive & ~edge)
+    need = contributing_tiles(prep, cam)
+    assert len(need) > 100
+    missing = [g for g in need if not vis[g] and not edge[g]]
+    assert not missing, missing[:10]
+    T = prep["T_view"].numpy()[vis]
+    got = rec[vis, :12].reshape(-1, 3, 4)
+    scale = np.abs(T).max(axis=(1, 2), keepdims=True)
+    assert np.max(np.abs(got - T) / scale) < 2e-5
+    np.testing.assert_allclose(rec[vis, 15], oh[vis], rtol=2e-5)
+    np.testing.assert_allclose(rec[vis, 12:15], prep["rgb"].numpy()[vis], atol=2e-5)
+    x0, y0, x1, y1 = rect_of(aux)
+    cx0, cy0, cx1, cy1 = contributing_extent(prep, cam)
+    seen = (cx0 <= cx1) & ~edge
+    assert seen.sum() > 100
+    assert np.all(x0[seen] <= cx0[seen]) and np.all(x1[seen] >= cx1[seen])
+    assert np.all(y0[seen] <= cy0[seen]) and np.all(y1[seen] >= cy1[seen])
+
+
 @pytest.mark.parametrize("wl,ci", CAMS)
 def test_cull_is_conservative_and_tight(wl, ci):
     scene, cams = scenes.workload(wl)
