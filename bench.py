@@ -40,7 +40,7 @@ OPS_PER_EVAL = 40
 # Mean DRAM bytes (read + write) of one render launch over the 16 poses of the
 # workload, from an ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum, cold cache; profiles/render_kernel_scene1m_1080p.md).
-RENDER_DRAM_BYTES = 16.20e6
+RENDER_DRAM_BYTES = 16.18e6
 FP32_LANES_PER_SM = 128
 
 
