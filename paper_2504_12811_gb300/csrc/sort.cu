@@ -303,6 +303,7 @@ __device__ __forceinline__ void sort_pass(const uint32_t* __restrict__ keys_in, 
   }
 }
 
+// the parameter list shared by the pass kernels below (those of sort_pass)
 #define AAAG_SORT_PASS_ARGS                                                                              \
   const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out, \
       uint32_t *__restrict__ vals_out, const uint32_t *__restrict__ n_dev, int64_t n_max, int pass,          \
